@@ -1,0 +1,345 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped filter,
+a wrong comparison in "lower" or in the canonical test, a transposed bit in
+the code, a missing relabeling) fails at least one of them:
+
+* closed forms: C(n,k) cliques in K_n, e_k(part sizes) in Turan graphs,
+  trace(A^3)/6 triangles, sum C(d,2) - 3T wedges, path/cycle/star/Petersen
+  motif counts, the star identity;
+* independent library routines: networkx clique enumeration, networkx
+  isomorphism classes over brute-forced k-subsets, the networkx graph atlas;
+* invariants: per-root sums, order independence, relabelling invariance,
+  all induced k-subsets summing to C(n,k);
+* the paper's k = 4 dictionary facts (Section 4.3.4) and the OEIS class
+  counts stored under tests/golden/.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2212_04551_gb300 import graphs as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_classes():
+    rows = {}
+    with open(os.path.join(GOLDEN, "graph_classes.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, c, a = (int(x) for x in line.split())
+            rows[k] = (c, a)
+    return rows
+
+
+def _adj_matrix(g) -> np.ndarray:
+    a = np.zeros((g.n, g.n), dtype=np.int64)
+    e = g.edges()
+    a[e[:, 0], e[:, 1]] = 1
+    a[e[:, 1], e[:, 0]] = 1
+    return a
+
+
+def _elem_sym(vals, k):
+    e = [1] + [0] * k
+    for x in vals:
+        for j in range(k, 0, -1):
+            e[j] += e[j - 1] * x
+    return e[k]
+
+
+def _random_small(seed, n=None, p=None):
+    rng = np.random.default_rng(1000 + seed)
+    n = n or int(rng.integers(5, 14))
+    p = p if p is not None else float(rng.uniform(0.15, 0.7))
+    return G.gnp(n, p, seed)
+
+
+# ------------------------------------------------------------------ cliques
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 13])
+def test_clique_complete_graph(n):
+    g = G.complete(n)
+    for k in range(1, min(n + 2, 14)):
+        assert O.clique_count(g, k) == comb(n, k)
+        assert O.clique_count(g, k, order=O.ORDER_DEGREE) == comb(n, k)
+
+
+def test_clique_empty_and_union():
+    assert O.clique_count(G.empty(7), 1) == 7
+    for k in range(2, 5):
+        assert O.clique_count(G.empty(7), k) == 0
+    g = G.disjoint_union(G.complete(6), G.complete(9), G.path(4))
+    for k in range(3, 10):
+        assert O.clique_count(g, k) == comb(6, k) + comb(9, k)
+    assert O.clique_count(g, 2) == 15 + 36 + 3
+
+
+@pytest.mark.parametrize("n,r", [(10, 3), (17, 4), (12, 12), (9, 2)])
+def test_clique_turan(n, r):
+    g = G.turan(n, r)
+    parts = [len(range(i, n, r)) for i in range(r)]
+    for k in range(1, r + 2):
+        assert O.clique_count(g, k) == _elem_sym(parts, k)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_triangles_trace(seed):
+    g = _random_small(seed, n=40, p=0.3)
+    a = _adj_matrix(g)
+    t = int(np.trace(a @ a @ a)) // 6
+    assert O.clique_count(g, 3) == t
+    assert O.clique_count(g, 3, order=O.ORDER_DEGREE) == t
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cliques_vs_networkx(seed):
+    nx = pytest.importorskip("networkx")
+    g = _random_small(seed, n=30, p=0.45)
+    h = nx.Graph()
+    h.add_nodes_from(range(g.n))
+    h.add_edges_from(map(tuple, g.edges()))
+    by_k: dict[int, int] = {}
+    first: dict[tuple[int, int], int] = {}
+    for c in nx.enumerate_all_cliques(h):
+        by_k[len(c)] = by_k.get(len(c), 0) + 1
+        key = (len(c), min(c))
+        first[key] = first.get(key, 0) + 1
+    for k in range(1, 9):
+        assert O.clique_count(g, k) == by_k.get(k, 0)
+        # per-root decomposition under the id order: root = smallest id
+        tot, pr = O.clique_count(g, k, per_root=True)
+        assert tot == by_k.get(k, 0)
+        assert [int(x) for x in pr] == [first.get((k, v), 0) for v in range(g.n)]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_clique_degree_order_per_root(seed):
+    nx = pytest.importorskip("networkx")
+    g = _random_small(seed, n=28, p=0.5)
+    d = g.degrees()
+    h = nx.Graph()
+    h.add_nodes_from(range(g.n))
+    h.add_edges_from(map(tuple, g.edges()))
+    for k in (3, 4, 5):
+        want = np.zeros(g.n, dtype=np.int64)
+        for c in nx.enumerate_all_cliques(h):
+            if len(c) == k:
+                want[min(c, key=lambda v: (d[v], v))] += 1
+        tot, pr = O.clique_count(g, k, order=O.ORDER_DEGREE, per_root=True)
+        assert tot == int(want.sum())
+        assert np.array_equal(pr.astype(np.int64), want)
+        # a root subset returns exactly those roots' counts
+        roots = np.arange(0, g.n, 3)
+        tot_s, pr_s = O.clique_count(g, k, order=O.ORDER_DEGREE, roots=roots, per_root=True)
+        assert tot_s == int(want[roots].sum())
+        assert np.array_equal(pr_s.astype(np.int64), want[roots])
+
+
+# -------------------------------------------------------- canonical codes
+
+def _atlas_by_k():
+    nx = pytest.importorskip("networkx")
+    out: dict[int, list] = {}
+    for h in nx.graph_atlas_g():
+        out.setdefault(h.number_of_nodes(), []).append(h)
+    return out
+
+
+def test_canon_is_complete_invariant_atlas():
+    """Distinct on non-isomorphic graphs, equal on relabelled copies, for every
+    graph on up to 7 vertices (networkx atlas), and the class counts match
+    OEIS A001349 / A000088."""
+    nx = pytest.importorskip("networkx")
+    golden = _golden_classes()
+    rng = np.random.default_rng(7)
+    atlas = _atlas_by_k()
+    for k in range(1, 8):
+        graphs = atlas[k]
+        codes = [O.full_code(h.edges(), k) for h in graphs]
+        canon = O.canon_many(k, codes)
+        assert len(set(canon.tolist())) == len(graphs) == golden[k][1]
+        n_conn = sum(1 for h in graphs if nx.is_connected(h))
+        assert n_conn == golden[k][0]
+        for h, c in zip(graphs, canon):
+            assert O.code_connected(k, int(c)) == nx.is_connected(h)
+        # relabelled copies
+        sample = range(0, len(graphs), max(1, len(graphs) // 60))
+        for i in sample:
+            h = graphs[i]
+            perm = rng.permutation(k)
+            e = [(int(perm[a]), int(perm[b])) for a, b in h.edges()]
+            assert O.canon(k, O.full_code(e, k)) == int(canon[i])
+
+
+def test_oracle_class_enumeration_matches_oeis():
+    golden = _golden_classes()
+    for k in range(1, 7):
+        assert len(O.classes(k, True)) == golden[k][0]
+        assert len(O.classes(k, False)) == golden[k][1]
+
+
+def test_paper_k4_dictionary():
+    """Section 4.3.4: k = 4 traversal bitmaps have 5 bits (v0-v1 implicit),
+    low two bits = v2's edges to (v0, v1), next three = v3's edges to
+    (v0, v1, v2).  Of the 32 codes, those where v2 and v3 each have an
+    earlier neighbour are connected traversals, and they reach exactly the
+    connected 4-vertex classes."""
+    meta = {}
+    with open(os.path.join(GOLDEN, "paper_k4_dictionary.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            meta[key] = [int(v) for v in vals]
+    assert meta["bits"] == [5] and meta["codes"] == [32]
+    golden = _golden_classes()
+    reps = set()
+    valid = 0
+    for t in range(meta["codes"][0]):
+        v2 = [(0, 2), (1, 2)]
+        v3 = [(0, 3), (1, 3), (2, 3)]
+        e = [(0, 1)]
+        e += [v2[b] for b in range(2) if (t >> b) & 1]
+        e += [v3[b] for b in range(3) if (t >> (2 + b)) & 1]
+        if (t & 0b11) == 0 or (t >> 2) == 0:
+            continue
+        valid += 1
+        c = O.canon(4, O.full_code(e, 4))
+        assert O.code_connected(4, c)
+        reps.add(c)
+    assert valid == 21
+    assert len(reps) == golden[4][0] == 6
+
+
+# ---------------------------------------------------------------- motifs
+
+def _nx_motifs(g, k):
+    """Brute force over k-subsets with networkx: {canonical code: count}."""
+    nx = pytest.importorskip("networkx")
+    h = nx.Graph()
+    h.add_nodes_from(range(g.n))
+    h.add_edges_from(map(tuple, g.edges()))
+    reps: list = []
+    counts: list[int] = []
+    for s in itertools.combinations(range(g.n), k):
+        sub = h.subgraph(s)
+        if not nx.is_connected(sub):
+            continue
+        for i, r in enumerate(reps):
+            if nx.is_isomorphic(sub, r):
+                counts[i] += 1
+                break
+        else:
+            reps.append(nx.convert_node_labels_to_integers(sub))
+            counts.append(1)
+    out = {}
+    for r, c in zip(reps, counts):
+        out[O.canon(k, O.full_code(r.edges(), k))] = c
+    return out
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_motifs_vs_networkx_bruteforce(seed):
+    g = _random_small(seed, n=11)
+    for k in (2, 3, 4, 5):
+        assert O.motif_count(g, k) == _nx_motifs(g, k)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_sums_to_binomial(seed):
+    g = _random_small(seed, n=14)
+    for k in (3, 4, 5, 6):
+        bf = O.brute_force(g, k)
+        assert sum(c for c, _ in bf.values()) == comb(g.n, k)
+        conn = {code: c for code, (c, is_conn) in bf.items() if is_conn}
+        assert conn == O.motif_count(g, k)
+        full = (1 << (k * (k - 1) // 2)) - 1
+        assert bf.get(full, (0, True))[0] == O.clique_count(g, k)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_k3_wedges_and_triangles(seed):
+    g = _random_small(seed, n=60, p=0.12)
+    a = _adj_matrix(g)
+    tri = int(np.trace(a @ a @ a)) // 6
+    d = g.degrees()
+    wedges = int(sum(comb(int(x), 2) for x in d)) - 3 * tri
+    got = O.motif_count(g, 3)
+    path3 = O.canon(3, O.full_code([(0, 1), (1, 2)], 3))
+    tri3 = O.canon(3, O.full_code([(0, 1), (1, 2), (0, 2)], 3))
+    assert got.get(path3, 0) == wedges
+    assert got.get(tri3, 0) == tri
+
+
+def _dominating(k, code):
+    """vertices adjacent to all others in the k-graph with this full code"""
+    adj = [[False] * k for _ in range(k)]
+    for i in range(1, k):
+        for j in range(i):
+            if (code >> (i * (i - 1) // 2 + j)) & 1:
+                adj[i][j] = adj[j][i] = True
+    return sum(1 for v in range(k) if all(adj[v][u] for u in range(k) if u != v))
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_star_identity(k):
+    """Every k-set containing a vertex and k-1 of its neighbours is connected,
+    so sum_p dom(p) * count_p = sum_v C(d(v), k-1)."""
+    g = G.sbm(120, 20, 0.35, 0.03, 11)
+    got = O.motif_count(g, k)
+    lhs = sum(_dominating(k, code) * c for code, c in got.items())
+    rhs = sum(comb(int(x), k - 1) for x in g.degrees())
+    assert lhs == rhs
+
+
+def test_structured_motifs():
+    star_k = lambda k: O.canon(k, O.full_code([(0, i) for i in range(1, k)], k))
+    path_k = lambda k: O.canon(k, O.full_code([(i, i + 1) for i in range(k - 1)], k))
+    cyc_k = lambda k: O.canon(k, O.full_code([(i, (i + 1) % k) for i in range(k)], k))
+    for n in (5, 9, 15):
+        for k in range(2, 7):
+            if k <= n:
+                assert O.motif_count(G.path(n), k) == {path_k(k): n - k + 1}
+            if k < n:
+                assert O.motif_count(G.cycle(n), k) == {path_k(k): n}
+        assert O.motif_count(G.cycle(n), n if n <= 8 else 8) == (
+            {cyc_k(n): 1} if n <= 8 else {path_k(8): n})
+    for s in (3, 7, 12):
+        for k in range(2, 7):
+            want = comb(s, k - 1)
+            assert O.motif_count(G.star(s), k) == ({star_k(k): want} if want else {})
+    pet = O.motif_count(G.petersen(), 4)
+    assert pet == {star_k(4): 10, path_k(4): 60}
+    assert O.motif_count(G.petersen(), 3) == {path_k(3): 30}
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_relabel_invariance(seed):
+    g = _random_small(seed, n=40, p=0.15)
+    perm = np.random.default_rng(seed).permutation(g.n)
+    h = G.relabel(g, perm)
+    for k in (3, 4, 5):
+        assert O.motif_count(g, k) == O.motif_count(h, k)
+        assert O.clique_count(g, k) == O.clique_count(h, k)
+
+
+def test_motif_per_root_sums():
+    g = _random_small(3, n=50, p=0.12)
+    for k in (3, 4, 5):
+        full, pr = O.motif_count(g, k, per_root=True)
+        assert int(pr.sum()) == sum(full.values())
+        a = O.motif_count(g, k, roots=np.arange(0, 25))
+        b = O.motif_count(g, k, roots=np.arange(25, 50))
+        merged = dict(a)
+        for c, v in b.items():
+            merged[c] = merged.get(c, 0) + v
+        assert merged == full
