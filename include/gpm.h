@@ -1,0 +1,191 @@
+/*
+ * gpm.h -- C ABI of libgpm: exact subgraph enumeration on one GB300 (sm_103a).
+ *
+ * The library counts k-vertex subgraphs of an undirected graph by repeated
+ * subgraph extension, the enumeration function E(G, tr, k) of the paper
+ * (Eq. 1): a traversal tr grows by one vertex of its neighbourhood
+ * N(tr) (Definition 1) until |tr| = k, and the output function A aggregates
+ * it.  Two applications are exported (Section 4.4, Algorithm 4):
+ *
+ *   - k-clique counting: A counts traversals whose vertices are pairwise
+ *     adjacent; aggregate_counter adds the number of valid last-level
+ *     extensions (Section 4.3.4);
+ *   - induced k-motif counting: A maps every connected induced k-vertex
+ *     subgraph to its canonical representative (pattern) and counts it per
+ *     pattern (aggregate_pattern, canonical relabelling by dictionary,
+ *     Section 4.3.4, Fig. 4).
+ *
+ * Conventions shared by every call:
+ *   - Graphs are undirected int32 CSR: indptr[n+1] (indptr[0] = 0,
+ *     non-decreasing), indices[indptr[n]]; each adjacency list sorted strictly
+ *     ascending, symmetric, no self-loops, no duplicates, ids in [0, n).
+ *   - Counts are exact uint64.  A true count >= 2^64 makes the call return
+ *     GPM_EOVERFLOW (never a wrapped value).
+ *   - Results are written only when the call returns GPM_OK.
+ *   - Host-result calls synchronise the graph's stream before returning.
+ *   - The library owns every device buffer it allocates; caller buffers are
+ *     only read (inputs) or written (outputs) during the call.
+ *   - No call aborts, traps or exits the process; failures are status codes
+ *     with a message from gpm_last_error().
+ *   - Calls on one gpm_graph must not run concurrently from several host
+ *     threads (the graph caches per-call device buffers).
+ */
+#ifndef GPM_H
+#define GPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPM_OK = 0,
+    GPM_EINVAL = 1,     /* bad argument or malformed graph                    */
+    GPM_ENOMEM = 2,     /* host or device allocation failed                   */
+    GPM_ECUDA = 3,      /* a CUDA runtime call failed                         */
+    GPM_ETIMEOUT = 4,   /* a bounded device wait ran out (work donation)      */
+    GPM_EOVERFLOW = 5,  /* a count does not fit in uint64                     */
+    GPM_ENOTIMPL = 6    /* the requested k or mode is not built               */
+} gpm_status;
+
+typedef struct gpm_graph gpm_graph; /* opaque, library-owned */
+
+/* gpm_graph_create flags */
+#define GPM_DEVICE_PTRS   1u  /* indptr/indices are device pointers (e.g. torch CUDA tensors) */
+#define GPM_SKIP_VALIDATE 2u  /* trust the caller: skip the CSR checks                      */
+
+/* applications (gpm_count_roots, gpm_sched_*) */
+#define GPM_APP_CLIQUE 0
+#define GPM_APP_MOTIF  1
+
+/* limits */
+#define GPM_CLIQUE_MAX_K 16
+#define GPM_MOTIF_MAX_K  7
+
+/*
+ * Copy an undirected CSR graph (Section 2; adjacency lists contiguous, as in
+ * Section 4.3.1) onto the device of the current CUDA context.
+ *   indptr  : n+1 int32 offsets; indices: indptr[n] int32 neighbour ids.
+ *             Host pointers unless flags has GPM_DEVICE_PTRS.  Both arrays
+ *             are COPIED; the caller keeps ownership and may free them when
+ *             the call returns.
+ *   n       : number of vertices, 0 <= n < 2^31.
+ *   stream  : cudaStream_t every later call on this graph runs on (NULL =
+ *             the legacy default stream).
+ *   out     : receives the new graph.
+ * Unless GPM_SKIP_VALIDATE, the CSR is checked on the device (sorted strictly
+ * ascending, ids in range, no self-loop, symmetric); a violation returns
+ * GPM_EINVAL.  Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA.
+ */
+gpm_status gpm_graph_create(const int32_t* indptr, const int32_t* indices, int32_t n,
+                            uint32_t flags, void* stream, gpm_graph** out);
+
+/* Free a graph and every device buffer it owns.  NULL is allowed. */
+void gpm_graph_destroy(gpm_graph* g);
+
+/* n and the number of undirected edges m (= indptr[n] / 2). */
+gpm_status gpm_graph_info(const gpm_graph* g, int32_t* n, int64_t* m, int32_t* max_degree);
+
+/*
+ * Number of k-cliques (Algorithm 4, clique counting; Section 4.4), 1 <= k <=
+ * GPM_CLIQUE_MAX_K.  k = 1 gives n and k = 2 gives m.  The enumeration runs on
+ * the degree-ordered orientation of G (each clique is reached once, from its
+ * lowest-(degree, id) vertex), which plays the role of the paper's "lower"
+ * filter.  out_count: host pointer to one uint64.
+ * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT, GPM_EOVERFLOW.
+ */
+gpm_status gpm_clique_count(gpm_graph* g, int k, uint64_t* out_count);
+
+/*
+ * Numbers of j-cliques for every j in [k_lo, k_hi] from ONE enumeration to
+ * depth k_hi (every level of the search is itself a clique of that size).
+ * counts: host array of k_hi - k_lo + 1 uint64.  3 <= k_lo <= k_hi <=
+ * GPM_CLIQUE_MAX_K.  Errors as gpm_clique_count.
+ */
+gpm_status gpm_clique_count_range(gpm_graph* g, int k_lo, int k_hi, uint64_t* counts);
+
+/*
+ * Per-pattern counts of connected induced k-vertex subgraphs (Algorithm 4,
+ * motif counting; aggregate_pattern, Section 4.3.4), 1 <= k <=
+ * GPM_MOTIF_MAX_K.  counts: host array of counts_len uint64, counts_len >=
+ * gpm_motif_num_patterns(k); entry p is the number of subgraphs whose
+ * canonical representative is pattern id p (see gpm_motif_pattern).
+ * Errors: GPM_EINVAL (also counts_len too small), GPM_ENOMEM, GPM_ECUDA,
+ * GPM_ETIMEOUT, GPM_EOVERFLOW.
+ */
+gpm_status gpm_motif_count(gpm_graph* g, int k, uint64_t* counts, int64_t counts_len);
+
+/*
+ * Number of connected k-vertex patterns (pattern ids are 0 .. *out - 1):
+ * 1, 1, 2, 6, 21, 112, 853 for k = 1 .. 7.
+ */
+gpm_status gpm_motif_num_patterns(int k, int64_t* out);
+
+/*
+ * Full adjacency code of pattern `id` at size k: bit i(i-1)/2 + j is set iff
+ * vertices j < i of the pattern are adjacent, and the code is the smallest
+ * over all relabellings (the canonical representative, Section 3).  Pattern
+ * ids are ordered by (number of edges, canonical code), ascending -- the
+ * contiguous identifiers of Section 4.3.4 ("(b) -> (c)" in Fig. 4).
+ */
+gpm_status gpm_motif_pattern(int k, int64_t id, uint64_t* adj_code);
+
+/*
+ * Exact partial counts over a set of roots: only the subgraphs whose root is
+ * listed.  The root of a clique is its lowest-(degree, id) vertex; the root
+ * of a connected motif subgraph is its smallest vertex id.  Disjoint root
+ * sets add up to the full count.
+ *   app      : GPM_APP_CLIQUE or GPM_APP_MOTIF.
+ *   roots    : host array of n_roots distinct vertex ids (NULL: all
+ *              vertices, n_roots ignored).
+ *   counts   : host array of counts_len uint64 (1 for cliques, the number
+ *              of patterns for motifs).
+ *   per_root : nullable host array of n_roots uint64: each root's total
+ *              (for motifs, summed over patterns).
+ * Errors as gpm_clique_count / gpm_motif_count.
+ */
+gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, int64_t n_roots,
+                           uint64_t* counts, int64_t counts_len, uint64_t* per_root);
+
+/*
+ * Scheduling knobs.  None of them can change a count; they change only how
+ * work is split and ordered (Section 4.3.5 replaced by in-kernel donation).
+ */
+typedef struct {
+    int32_t warps_per_block;   /* 4, 8, 16 or 32 (0 = default 8)                       */
+    int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum)       */
+    int32_t donate_min;        /* split a level only if >= this many siblings remain  */
+    int32_t order;             /* GPM_ORDER_* root order of the plain scheduler         */
+    int32_t max_idle_ms;       /* bounded wait: an idle warp gives up after this long  */
+                               /* without any progress anywhere (GPM_ETIMEOUT)         */
+    int32_t donate;            /* 0 disables work donation                             */
+} gpm_config;
+
+#define GPM_ORDER_ID          0  /* roots in id order                               */
+#define GPM_ORDER_DEGREE_DESC 1  /* heaviest (largest out-/degree) roots first       */
+#define GPM_ORDER_CUSTOM      2  /* order set by gpm_sched_set_order                 */
+
+gpm_status gpm_get_config(const gpm_graph* g, gpm_config* out);
+gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg);
+
+/* Statistics of the last counting call on g (device-measured). */
+typedef struct {
+    double   kernel_ms;        /* enumeration kernel time (CUDA events)          */
+    uint64_t units_done;       /* work units (roots + donated units) finished     */
+    uint64_t donations;        /* units pushed to the donation queue              */
+    uint64_t idle_polls;       /* times an idle warp polled the queue             */
+    int32_t  grid_blocks;      /* persistent grid size                            */
+    int32_t  warps_per_block;
+} gpm_stats;
+
+gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* gpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPM_H */

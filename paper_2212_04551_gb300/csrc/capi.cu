@@ -1,0 +1,233 @@
+// capi.cu -- the extern "C" boundary of libgpm (declared in include/gpm.h).
+//
+// Every entry point validates its arguments, runs the work on the graph's
+// stream, synchronises before handing host results back, and maps internal
+// failures to a gpm_status plus a thread-local message.  No exception, abort
+// or trap crosses this boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gpm {
+gpm_graph* create_graph(const int32_t* indptr, const int32_t* indices, int32_t n, uint32_t flags, void* stream);
+void destroy_graph(gpm_graph* g);
+const char* last_error_cstr();
+}  // namespace gpm
+
+using namespace gpm;
+
+template <class F>
+static gpm_status guarded(F&& f) {
+    try {
+        clear_error();
+        f();
+        return GPM_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return GPM_ENOMEM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return GPM_ECUDA;
+    }
+}
+
+// Copy a host root list to the device (validated), or pass NULL through.
+static const int32_t* upload_roots(gpm_graph* g, const int32_t* roots, int64_t n_roots) {
+    if (!roots) return nullptr;
+    if (n_roots < 0) fail(GPM_EINVAL, "n_roots < 0");
+    for (int64_t i = 0; i < n_roots; i++)
+        if (roots[i] < 0 || roots[i] >= g->n) fail(GPM_EINVAL, "root id out of range");
+    g->roots_tmp.ensure(sizeof(int32_t) * std::max<int64_t>(n_roots, 1));
+    if (n_roots > 0)
+        GPM_CUDA(cudaMemcpyAsync(g->roots_tmp.ptr, roots, sizeof(int32_t) * n_roots, cudaMemcpyHostToDevice,
+                                 g->stream));
+    return g->roots_tmp.as<int32_t>();
+}
+
+static void check_graph(const gpm_graph* g) {
+    if (!g) fail(GPM_EINVAL, "graph is NULL");
+}
+
+static const int32_t* custom_or_null(gpm_graph* g, int64_t* n_roots) {
+    if (g->cfg.order == GPM_ORDER_CUSTOM) {
+        if (g->order_custom_len <= 0) fail(GPM_EINVAL, "GPM_ORDER_CUSTOM is selected but no root order was set");
+        *n_roots = g->order_custom_len;
+        return g->order_custom.as<int32_t>();
+    }
+    if (g->cfg.order == GPM_ORDER_ID) {
+        *n_roots = g->n;
+        return ensure_id_order(g);
+    }
+    return nullptr;   // heaviest-first order, chosen per application
+}
+
+extern "C" {
+
+gpm_status gpm_graph_create(const int32_t* indptr, const int32_t* indices, int32_t n, uint32_t flags,
+                            void* stream, gpm_graph** out) {
+    return guarded([&] {
+        if (!out) fail(GPM_EINVAL, "out is NULL");
+        *out = nullptr;
+        *out = create_graph(indptr, indices, n, flags, stream);
+    });
+}
+
+void gpm_graph_destroy(gpm_graph* g) {
+    try {
+        destroy_graph(g);
+    } catch (...) {
+    }
+}
+
+gpm_status gpm_graph_info(const gpm_graph* g, int32_t* n, int64_t* m, int32_t* max_degree) {
+    return guarded([&] {
+        check_graph(g);
+        if (n) *n = g->n;
+        if (m) *m = g->nnz / 2;
+        if (max_degree) *max_degree = g->max_deg;
+    });
+}
+
+gpm_status gpm_clique_count(gpm_graph* g, int k, uint64_t* out_count) {
+    return guarded([&] {
+        check_graph(g);
+        if (!out_count) fail(GPM_EINVAL, "out_count is NULL");
+        if (k < 1 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "k out of range [1, 16]");
+        int64_t nr = 0;
+        const int32_t* roots = custom_or_null(g, &nr);
+        uint64_t c = 0;
+        run_clique(g, k, k, roots, nr, nullptr, &c);
+        *out_count = c;
+    });
+}
+
+gpm_status gpm_clique_count_range(gpm_graph* g, int k_lo, int k_hi, uint64_t* counts) {
+    return guarded([&] {
+        check_graph(g);
+        if (!counts) fail(GPM_EINVAL, "counts is NULL");
+        if (k_lo < 3 || k_hi > GPM_CLIQUE_MAX_K || k_lo > k_hi) fail(GPM_EINVAL, "need 3 <= k_lo <= k_hi <= 16");
+        int64_t nr = 0;
+        const int32_t* roots = custom_or_null(g, &nr);
+        std::vector<uint64_t> c(k_hi - k_lo + 1, 0);
+        run_clique(g, k_lo, k_hi, roots, nr, nullptr, c.data());
+        std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
+    });
+}
+
+gpm_status gpm_motif_count(gpm_graph* g, int k, uint64_t* counts, int64_t counts_len) {
+    return guarded([&] {
+        check_graph(g);
+        if (!counts) fail(GPM_EINVAL, "counts is NULL");
+        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+        const PatternTable& t = pattern_table(k);
+        if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
+        int64_t nr = 0;
+        const int32_t* roots = custom_or_null(g, &nr);
+        std::vector<uint64_t> c(t.num_patterns, 0);
+        run_motif(g, k, roots, nr, nullptr, c.data());
+        std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
+    });
+}
+
+gpm_status gpm_motif_num_patterns(int k, int64_t* out) {
+    return guarded([&] {
+        if (!out) fail(GPM_EINVAL, "out is NULL");
+        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+        *out = pattern_table(k).num_patterns;
+    });
+}
+
+gpm_status gpm_motif_pattern(int k, int64_t id, uint64_t* adj_code) {
+    return guarded([&] {
+        if (!adj_code) fail(GPM_EINVAL, "adj_code is NULL");
+        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+        const PatternTable& t = pattern_table(k);
+        if (id < 0 || id >= t.num_patterns) fail(GPM_EINVAL, "pattern id out of range");
+        *adj_code = t.pattern_code[(size_t)id];
+    });
+}
+
+gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, int64_t n_roots,
+                           uint64_t* counts, int64_t counts_len, uint64_t* per_root) {
+    return guarded([&] {
+        check_graph(g);
+        if (!counts) fail(GPM_EINVAL, "counts is NULL");
+        if (app != GPM_APP_CLIQUE && app != GPM_APP_MOTIF) fail(GPM_EINVAL, "unknown app");
+        const int64_t nr = roots ? n_roots : g->n;
+        const int32_t* d_roots = upload_roots(g, roots, n_roots);
+        if (!d_roots) {
+            // all vertices in id order
+            std::vector<int32_t> all(g->n);
+            for (int32_t v = 0; v < g->n; v++) all[v] = v;
+            d_roots = upload_roots(g, all.data(), g->n);
+        }
+        unsigned long long* d_pr = nullptr;
+        if (per_root) {
+            g->per_root_tmp.ensure(sizeof(unsigned long long) * std::max<int64_t>(nr, 1));
+            d_pr = g->per_root_tmp.as<unsigned long long>();
+        }
+        std::vector<uint64_t> c;
+        if (app == GPM_APP_CLIQUE) {
+            if (k < 1 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "k out of range [1, 16]");
+            if (counts_len < 1) fail(GPM_EINVAL, "counts_len < 1");
+            c.assign(1, 0);
+            run_clique(g, k, k, d_roots, nr, d_pr, c.data());
+        } else {
+            if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+            const PatternTable& t = pattern_table(k);
+            if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
+            c.assign(t.num_patterns, 0);
+            run_motif(g, k, d_roots, nr, d_pr, c.data());
+        }
+        if (per_root && nr > 0) {
+            GPM_CUDA(cudaMemcpyAsync(per_root, d_pr, sizeof(uint64_t) * nr, cudaMemcpyDeviceToHost, g->stream));
+            GPM_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
+    });
+}
+
+gpm_status gpm_get_config(const gpm_graph* g, gpm_config* out) {
+    return guarded([&] {
+        check_graph(g);
+        if (!out) fail(GPM_EINVAL, "out is NULL");
+        *out = g->cfg;
+    });
+}
+
+gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
+    return guarded([&] {
+        check_graph(g);
+        if (!cfg) fail(GPM_EINVAL, "cfg is NULL");
+        gpm_config c = *cfg;
+        if (c.warps_per_block == 0) c.warps_per_block = 8;
+        if (c.warps_per_block != 1 && c.warps_per_block != 2 && c.warps_per_block != 4 &&
+            c.warps_per_block != 8 && c.warps_per_block != 16 && c.warps_per_block != 32)
+            fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 32]");
+        if (c.blocks_per_sm < 0) fail(GPM_EINVAL, "blocks_per_sm < 0");
+        if (c.donate_min < 0) fail(GPM_EINVAL, "donate_min < 0");
+        if (c.order < GPM_ORDER_ID || c.order > GPM_ORDER_CUSTOM) fail(GPM_EINVAL, "unknown order");
+        if (c.max_idle_ms <= 0) fail(GPM_EINVAL, "max_idle_ms must be positive");
+        g->cfg = c;
+    });
+}
+
+gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out) {
+    return guarded([&] {
+        check_graph(g);
+        if (!out) fail(GPM_EINVAL, "out is NULL");
+        *out = g->stats;
+    });
+}
+
+const char* gpm_last_error(void) { return last_error_cstr(); }
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// common.cuh -- internal declarations shared by the libgpm CUDA sources.
+//
+// Nothing here is part of the public ABI (include/gpm.h).  The library is
+// single-GPU: every device buffer of a gpm_graph lives on the device that was
+// current when the graph was created, and every kernel runs on the graph's
+// stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gpm.h"
+
+namespace gpm {
+
+// ------------------------------------------------------------------ errors
+
+// Thread-local message of the last failure (gpm_last_error()).
+void set_error(const std::string& msg);
+void clear_error();
+
+struct Error {
+    gpm_status status;
+    std::string msg;
+};
+
+// Throwing is internal only: every extern "C" entry point catches and maps
+// to a status, so no exception crosses the ABI.
+[[noreturn]] void fail(gpm_status s, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define GPM_CUDA(call) ::gpm::check_cuda((call), #call)
+
+// --------------------------------------------------------- device buffers
+
+// Grow-only device allocation owned by a graph.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    ~DevBuf();
+    void ensure(size_t need);   // may reallocate (contents lost)
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// -------------------------------------------------------------- the graph
+
+struct DagView {
+    const int32_t* off = nullptr;    // n+1 offsets, every list padded to a multiple of 4
+    const int32_t* adj = nullptr;    // out-neighbours (higher (degree, id)), sorted by id
+    const int32_t* outdeg = nullptr; // n exact out-degrees
+    int32_t max_outdeg = 0;
+};
+
+}  // namespace gpm
+
+struct gpm_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t n = 0;
+    int64_t nnz = 0;            // indptr[n] = 2m
+    int32_t max_deg = 0;
+    int num_sms = 0;
+
+    gpm::DevBuf indptr, indices, degree;
+
+    // degree-ordered DAG (built on the first clique call)
+    bool dag_ready = false;
+    gpm::DevBuf dag_off, dag_adj, dag_outdeg;
+    int32_t max_outdeg = 0;
+
+    // root orders of the plain scheduler (built lazily)
+    bool order_motif_ready = false, order_clique_ready = false;
+    gpm::DevBuf order_motif, order_clique;
+    bool order_id_ready = false;
+    gpm::DevBuf order_id;
+    // custom root order (learned scheduler or caller)
+    gpm::DevBuf order_custom;
+    int64_t order_custom_len = 0;
+
+    // per-call scratch, grown on demand
+    gpm::DevBuf scratch_small;     // counters, flags, queue control
+    gpm::DevBuf scratch_queue;     // donation ring
+    gpm::DevBuf scratch_slab;      // per-warp DFS stacks (extension arrays)
+    gpm::DevBuf scratch_mark;      // per-warp vertex marks (motif)
+    size_t mark_bytes_cleared = 0;
+    gpm::DevBuf roots_tmp;         // caller root lists
+    gpm::DevBuf per_root_tmp;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    gpm_config cfg{};
+    gpm_stats stats{};
+};
+
+namespace gpm {
+
+// --------------------------------------------------------- shared control
+
+// Control block of one persistent enumeration launch (device memory).
+struct Control {
+    unsigned long long counts[GPM_CLIQUE_MAX_K + 1];  // per clique size (clique kernel)
+    unsigned long long next_root;     // next index into the root list
+    long long pending;                // roots + donated units not yet finished
+    int idle;                         // warps currently without work
+    int error;                        // GPM_* status raised on the device
+    unsigned long long q_head, q_tail;
+    unsigned long long donations, units_done, idle_polls;
+    int overflow;
+    int pad;
+};
+
+// Device-side status values (mirrors gpm_status).
+enum : int { DEV_OK = 0, DEV_ETIMEOUT = GPM_ETIMEOUT, DEV_EOVERFLOW = GPM_EOVERFLOW,
+             DEV_EINVAL = GPM_EINVAL };
+
+// Launch geometry for a persistent kernel.
+struct Grid {
+    int blocks = 0;
+    int warps_per_block = 0;
+    int total_warps() const { return blocks * warps_per_block; }
+};
+
+// graph.cu
+void ensure_dag(gpm_graph* g);
+const int32_t* ensure_root_order(gpm_graph* g, int app);  // plain scheduler order
+const int32_t* ensure_id_order(gpm_graph* g);             // 0, 1, ..., n-1
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total,
+                        cudaStream_t s, DevBuf& tmp);
+
+// lut.cpp (host pattern dictionary)
+struct PatternTable {
+    int k = 0;
+    int64_t num_patterns = 0;
+    std::vector<uint64_t> pattern_code;   // canonical full code of each pattern id
+    std::vector<uint16_t> lut;            // traversal code -> pattern id (0xFFFF invalid)
+};
+const PatternTable& pattern_table(int k);  // built once per k, cached
+const uint16_t* device_lut(int k);         // uploaded once per (device, k)
+
+// clique.cu / motif.cu
+void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
+                unsigned long long* d_per_root, uint64_t* counts_out);
+void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
+               unsigned long long* d_per_root, uint64_t* counts_out);
+
+// helpers
+int resident_blocks(const void* kernel, int threads, size_t smem);
+Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block);
+gpm_config default_config();
+
+}  // namespace gpm
+
+#ifdef __CUDACC__
+// ----------------------------------------------------------- device helpers
+
+#define GPM_FULL_MASK 0xffffffffu
+
+__device__ __forceinline__ unsigned long long gpm_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned gpm_lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <class T>
+__device__ __forceinline__ T gpm_warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GPM_FULL_MASK, v, o);
+    return v;
+}
+
+// ------------------------------------------------- donation queue (device)
+//
+// Bounded multi-producer multi-consumer ring of sequence-numbered slots
+// (after D. Vyukov's bounded MPMC queue).  Slot i starts with seq = i.  A
+// producer reserves position p (seq == p), writes the unit -- and any payload
+// kept beside the ring at index p % cap -- and publishes seq = p + 1.  A
+// consumer claims p (seq == p + 1), reads, and releases with seq = p + cap.
+// Every loop is bounded: a full, empty or contended queue reports failure
+// and the caller keeps (or goes on looking for) work.  Reads of published
+// data go through L2 (ld.global.cg): L1 is not coherent across SMs.
+struct QSeq {
+    unsigned long long seq;
+};
+
+namespace gpm {
+__global__ void k_queue_init(QSeq* q, unsigned long long cap);
+}
+
+__device__ __forceinline__ bool gpm_q_reserve(QSeq* q, unsigned long long cap, unsigned long long* tail,
+                                              unsigned long long* out_pos) {
+    unsigned long long pos = *(volatile unsigned long long*)tail;
+    for (int tries = 0; tries < 256; tries++) {
+        const unsigned long long seq = *(volatile unsigned long long*)&q[pos % cap].seq;
+        const long long dif = (long long)(seq - pos);
+        if (dif == 0) {
+            const unsigned long long prev = atomicCAS(tail, pos, pos + 1);
+            if (prev == pos) {
+                *out_pos = pos;
+                return true;
+            }
+            pos = prev;
+        } else if (dif < 0) {
+            return false;  // full
+        } else {
+            pos = *(volatile unsigned long long*)tail;
+        }
+    }
+    return false;
+}
+
+// call after every writer of the slot's data has executed __threadfence()
+__device__ __forceinline__ void gpm_q_publish(QSeq* q, unsigned long long cap, unsigned long long pos) {
+    atomicExch(&q[pos % cap].seq, pos + 1);
+}
+
+__device__ __forceinline__ bool gpm_q_claim(QSeq* q, unsigned long long cap, unsigned long long* head,
+                                            unsigned long long* out_pos) {
+    unsigned long long pos = *(volatile unsigned long long*)head;
+    for (int tries = 0; tries < 256; tries++) {
+        const unsigned long long seq = *(volatile unsigned long long*)&q[pos % cap].seq;
+        const long long dif = (long long)(seq - (pos + 1));
+        if (dif == 0) {
+            const unsigned long long prev = atomicCAS(head, pos, pos + 1);
+            if (prev == pos) {
+                __threadfence();
+                *out_pos = pos;
+                return true;
+            }
+            pos = prev;
+        } else if (dif < 0) {
+            return false;  // empty
+        } else {
+            pos = *(volatile unsigned long long*)head;
+        }
+    }
+    return false;
+}
+
+// call after every reader of the slot's data is done (and fenced)
+__device__ __forceinline__ void gpm_q_release(QSeq* q, unsigned long long cap, unsigned long long pos) {
+    atomicExch(&q[pos % cap].seq, pos + cap);
+}
+
+// word-wise L2 copy of a published POD record
+template <class U>
+__device__ __forceinline__ void gpm_load_cg(U* dst, const U* src) {
+    static_assert(sizeof(U) % 4 == 0, "record size must be a multiple of 4 bytes");
+    const unsigned* s = reinterpret_cast<const unsigned*>(src);
+    unsigned* d = reinterpret_cast<unsigned*>(dst);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(U) / 4); i++) d[i] = __ldcg(s + i);
+}
+
+#endif  // __CUDACC__

@@ -1,0 +1,259 @@
+"""Thin Python binding of libgpm (include/gpm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does no
+counting of its own: all enumeration runs in the CUDA kernels of libgpm.so.
+If the library cannot be loaded the import-time ``load()`` raises; there is
+no CPU fallback.
+
+Arrays may be numpy (host) or torch tensors (host or CUDA); CUDA tensors are
+passed to the library as device pointers (GPM_DEVICE_PTRS).  Streams may be a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None (the legacy
+default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GPM_OK, GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT, GPM_EOVERFLOW, GPM_ENOTIMPL = range(7)
+STATUS_NAMES = {0: "GPM_OK", 1: "GPM_EINVAL", 2: "GPM_ENOMEM", 3: "GPM_ECUDA", 4: "GPM_ETIMEOUT",
+                5: "GPM_EOVERFLOW", 6: "GPM_ENOTIMPL"}
+GPM_DEVICE_PTRS = 1
+GPM_SKIP_VALIDATE = 2
+GPM_APP_CLIQUE = 0
+GPM_APP_MOTIF = 1
+GPM_ORDER_ID = 0
+GPM_ORDER_DEGREE_DESC = 1
+GPM_ORDER_CUSTOM = 2
+GPM_CLIQUE_MAX_K = 16
+GPM_MOTIF_MAX_K = 7
+
+
+class GpmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gpm_config(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("donate_min", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32)]
+
+
+class gpm_stats(ctypes.Structure):
+    _fields_ = [("kernel_ms", ctypes.c_double), ("units_done", ctypes.c_uint64),
+                ("donations", ctypes.c_uint64), ("idle_polls", ctypes.c_uint64),
+                ("grid_blocks", ctypes.c_int32), ("warps_per_block", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); every symbol include/gpm.h declares
+SIGNATURES = {
+    "gpm_graph_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]),
+    "gpm_graph_destroy": (None, [_vp]),
+    "gpm_graph_info": (ctypes.c_int, [_vp, _i32p, _i64p, _i32p]),
+    "gpm_clique_count": (ctypes.c_int, [_vp, ctypes.c_int, _u64p]),
+    "gpm_clique_count_range": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p]),
+    "gpm_motif_count": (ctypes.c_int, [_vp, ctypes.c_int, _u64p, ctypes.c_int64]),
+    "gpm_motif_num_patterns": (ctypes.c_int, [ctypes.c_int, _i64p]),
+    "gpm_motif_pattern": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _u64p]),
+    "gpm_count_roots": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int64, _u64p,
+                                       ctypes.c_int64, _u64p]),
+    "gpm_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
+    "gpm_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
+    "gpm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
+    "gpm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgpm.so (building it first if asked); raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgpm is not built ({path}); run paper_2212_04551_gb300/build.py")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != GPM_OK:
+        msg = load().gpm_last_error()
+        raise GpmError(status, where, msg.decode() if msg else "")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _array_ptr(a, dtype):
+    """(pointer, keepalive, is_device) for a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != (torch.int32 if dtype == np.int32 else torch.uint64):
+                raise TypeError(f"expected {dtype}, got {a.dtype}")
+            a = a.contiguous()
+            return a.data_ptr(), a, a.is_cuda
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.size == 0:
+        arr = np.zeros(1, dtype=dtype)
+    return arr.ctypes.data, arr, False
+
+
+class Graph:
+    """Owning handle of a gpm_graph (destroyed with the object)."""
+
+    def __init__(self, handle: int, keep=()):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gpm_graph_destroy(self)
+            self.handle = None
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+
+# ------------------------------------------------------------- entry points
+
+def gpm_graph_create(indptr, indices, n: int | None = None, flags: int = 0, stream=None) -> Graph:
+    lib = load()
+    pi, ki, dev_i = _array_ptr(indptr, np.int32)
+    px, kx, dev_x = _array_ptr(indices, np.int32)
+    if dev_i != dev_x:
+        raise ValueError("indptr and indices must both be host or both be device arrays")
+    if dev_i:
+        flags |= GPM_DEVICE_PTRS
+    if n is None:
+        n = int(indptr.shape[0]) - 1
+    out = ctypes.c_void_p()
+    st = lib.gpm_graph_create(pi, px, int(n), int(flags), _stream_handle(stream), ctypes.byref(out))
+    _check(st, "gpm_graph_create")
+    return Graph(out.value, keep=(ki, kx))
+
+
+def gpm_graph_destroy(g: Graph) -> None:
+    load().gpm_graph_destroy(ctypes.c_void_p(g.handle))
+
+
+def gpm_graph_info(g: Graph) -> tuple[int, int, int]:
+    n = ctypes.c_int32()
+    m = ctypes.c_int64()
+    d = ctypes.c_int32()
+    _check(load().gpm_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d)), "gpm_graph_info")
+    return n.value, m.value, d.value
+
+
+def gpm_clique_count(g: Graph, k: int) -> int:
+    out = ctypes.c_uint64()
+    _check(load().gpm_clique_count(g, int(k), ctypes.byref(out)), "gpm_clique_count")
+    return out.value
+
+
+def gpm_clique_count_range(g: Graph, k_lo: int, k_hi: int) -> list[int]:
+    out = (ctypes.c_uint64 * (k_hi - k_lo + 1))()
+    _check(load().gpm_clique_count_range(g, int(k_lo), int(k_hi), out), "gpm_clique_count_range")
+    return [int(x) for x in out]
+
+
+def gpm_motif_num_patterns(k: int) -> int:
+    out = ctypes.c_int64()
+    _check(load().gpm_motif_num_patterns(int(k), ctypes.byref(out)), "gpm_motif_num_patterns")
+    return out.value
+
+
+def gpm_motif_pattern(k: int, pid: int) -> int:
+    out = ctypes.c_uint64()
+    _check(load().gpm_motif_pattern(int(k), int(pid), ctypes.byref(out)), "gpm_motif_pattern")
+    return out.value
+
+
+def gpm_motif_count(g: Graph, k: int) -> np.ndarray:
+    npat = gpm_motif_num_patterns(k)
+    out = np.zeros(npat, dtype=np.uint64)
+    _check(load().gpm_motif_count(g, int(k), out.ctypes.data_as(_u64p), npat), "gpm_motif_count")
+    return out
+
+
+def gpm_count_roots(g: Graph, app: int, k: int, roots=None, per_root: bool = False):
+    """Exact counts over a root subset: (counts, per_root or None)."""
+    ncounts = 1 if app == GPM_APP_CLIQUE else gpm_motif_num_patterns(k)
+    counts = np.zeros(ncounts, dtype=np.uint64)
+    if roots is None:
+        rp, nr = None, 0
+        nrep = gpm_graph_info(g)[0]
+    else:
+        r = np.ascontiguousarray(roots, dtype=np.int32)
+        rp, nr, nrep = r.ctypes.data_as(_i32p), int(r.shape[0]), int(r.shape[0])
+    pr = np.zeros(max(nrep, 1), dtype=np.uint64) if per_root else None
+    st = load().gpm_count_roots(g, int(app), int(k), rp, nr, counts.ctypes.data_as(_u64p), ncounts,
+                                pr.ctypes.data_as(_u64p) if pr is not None else None)
+    _check(st, "gpm_count_roots")
+    return counts, (pr[:nrep] if pr is not None else None)
+
+
+def gpm_get_config(g: Graph) -> gpm_config:
+    c = gpm_config()
+    _check(load().gpm_get_config(g, ctypes.byref(c)), "gpm_get_config")
+    return c
+
+
+def gpm_set_config(g: Graph, cfg: gpm_config | None = None, **kw) -> None:
+    c = cfg if cfg is not None else gpm_get_config(g)
+    for key, val in kw.items():
+        setattr(c, key, int(val))
+    _check(load().gpm_set_config(g, ctypes.byref(c)), "gpm_set_config")
+
+
+def gpm_get_stats(g: Graph) -> dict:
+    s = gpm_stats()
+    _check(load().gpm_get_stats(g, ctypes.byref(s)), "gpm_get_stats")
+    return {f: getattr(s, f) for f, _ in gpm_stats._fields_}
+
+
+def gpm_last_error() -> str:
+    m = load().gpm_last_error()
+    return m.decode() if m else ""
+
+
+def graph_from_csr(csr, stream=None, flags: int = 0) -> Graph:
+    """Create a device graph from a ``graphs.CSR`` (host arrays)."""
+    return gpm_graph_create(csr.indptr, csr.indices, csr.n, flags=flags, stream=stream)

@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Counts are integers, so the bar is bit-exact equality.  Motif counts are
+compared per pattern: the library's pattern id p is mapped to its canonical
+code with gpm_motif_pattern, and the oracle reports counts keyed by the same
+canonical code (its own relabelling minimum).
+"""
+from __future__ import annotations
+
+import json
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2212_04551_gb300 import gpm
+from paper_2212_04551_gb300 import graphs as G
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gpm.load()
+    O.build()
+
+
+def motif_by_code(g_dev, k) -> dict[int, int]:
+    counts = gpm.gpm_motif_count(g_dev, k)
+    return {gpm.gpm_motif_pattern(k, p): int(c) for p, c in enumerate(counts) if c}
+
+
+def random_graph(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(2, 90))
+    p = float(rng.uniform(0.02, 0.5))
+    return G.gnp(n, p, seed)
+
+
+# -------------------------------------------------------------- small graphs
+
+@pytest.mark.parametrize("seed", range(40))
+def test_clique_random_graphs(seed):
+    g = random_graph(seed)
+    dg = gpm.graph_from_csr(g)
+    for k in range(1, 9):
+        assert gpm.gpm_clique_count(dg, k) == O.clique_count(g, k), (seed, k)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_motif_random_graphs(seed):
+    g = random_graph(seed)
+    dg = gpm.graph_from_csr(g)
+    kmax = 6 if g.m < 600 else 5
+    for k in range(1, kmax + 1):
+        assert motif_by_code(dg, k) == O.motif_count(g, k), (seed, k)
+
+
+def test_motif_k7_random():
+    for seed in range(4):
+        g = G.gnp(40, 0.12, 900 + seed)
+        dg = gpm.graph_from_csr(g)
+        assert motif_by_code(dg, 7) == O.motif_count(g, 7)
+
+
+def test_edge_cases():
+    # empty graph, a single vertex, isolated vertices
+    for g in (G.empty(0), G.empty(1), G.empty(17)):
+        dg = gpm.graph_from_csr(g)
+        assert gpm.gpm_clique_count(dg, 1) == g.n
+        for k in (2, 3, 5):
+            assert gpm.gpm_clique_count(dg, k) == 0
+        assert int(gpm.gpm_motif_count(dg, 1)[0]) == g.n
+        for k in (2, 3, 4):
+            assert int(gpm.gpm_motif_count(dg, k).sum()) == 0
+    # k above the largest clique; k = 2 gives m
+    g = G.disjoint_union(G.complete(5), G.path(7), G.empty(3))
+    dg = gpm.graph_from_csr(g)
+    assert gpm.gpm_clique_count(dg, 6) == 0
+    assert gpm.gpm_clique_count(dg, 2) == g.m
+    assert gpm.gpm_clique_count(dg, 5) == 1
+
+
+@pytest.mark.parametrize("n", [2, 33, 64, 65, 130, 300])
+def test_complete_graphs(n):
+    """K_n forces one full bitmap root of n-1 columns (multi-word rows)."""
+    dg = gpm.graph_from_csr(G.complete(n))
+    for k in (3, 4, 5):
+        assert gpm.gpm_clique_count(dg, k) == comb(n, k)
+    if n <= 65:
+        for k in (6, 7):
+            assert gpm.gpm_clique_count(dg, k) == comb(n, k)
+    if n <= 64:
+        got = gpm.gpm_motif_count(dg, 4)
+        assert int(got.sum()) == comb(n, 4) and int(got[-1]) == comb(n, 4)
+
+
+def test_turan_and_union():
+    g = G.turan(60, 5)
+    dg = gpm.graph_from_csr(g)
+    parts = [12] * 5
+    for k in range(1, 7):
+        e = [1] + [0] * k
+        for x in parts:
+            for j in range(k, 0, -1):
+                e[j] += e[j - 1] * x
+        assert gpm.gpm_clique_count(dg, k) == e[k]
+
+
+def test_star_with_large_hub():
+    """A hub of degree 300 (motifs) -- a long exclusive list in one step."""
+    g = G.star(300)
+    dg = gpm.graph_from_csr(g)
+    for k in (2, 3, 4):
+        got = gpm.gpm_motif_count(dg, k)
+        assert int(got.sum()) == comb(300, k - 1)
+    assert motif_by_code(dg, 4) == O.motif_count(g, 4)
+
+
+def test_padding_boundaries():
+    """Out-lists whose lengths straddle the 4-entry padding of the oriented CSR."""
+    parts = [G.complete(s) for s in (3, 4, 5, 6, 7, 8, 9)]
+    g = G.disjoint_union(*parts, G.path(11), G.cycle(13))
+    dg = gpm.graph_from_csr(g)
+    for k in range(3, 9):
+        assert gpm.gpm_clique_count(dg, k) == O.clique_count(g, k)
+    for k in (3, 4, 5):
+        assert motif_by_code(dg, k) == O.motif_count(g, k)
+
+
+def test_clique_range_matches_single():
+    g = G.sbm(400, 50, 0.45, 0.02, 77)
+    dg = gpm.graph_from_csr(g)
+    rng_counts = gpm.gpm_clique_count_range(dg, 3, 9)
+    for k in range(3, 10):
+        assert rng_counts[k - 3] == O.clique_count(g, k)
+
+
+# ---------------------------------------------------------- per-root parity
+
+def test_per_root_clique_and_motif():
+    g = G.gnp(70, 0.2, 123)
+    dg = gpm.graph_from_csr(g)
+    roots = np.arange(0, 70, 3, dtype=np.int32)
+    for k in (3, 4, 5):
+        c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, k, roots, per_root=True)
+        tot, opr = O.clique_count(g, k, order=O.ORDER_DEGREE, roots=roots, per_root=True)
+        assert int(c[0]) == tot and np.array_equal(pr, opr)
+        c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, k, roots, per_root=True)
+        want, opr = O.motif_count(g, k, roots=roots, per_root=True)
+        got = {gpm.gpm_motif_pattern(k, p): int(x) for p, x in enumerate(c) if x}
+        assert got == want and np.array_equal(pr, opr)
+
+
+# -------------------------------------------------- scheduler independence
+
+@pytest.mark.parametrize("cfg", [
+    dict(donate=0), dict(donate=1, donate_min=2), dict(warps_per_block=4),
+    dict(warps_per_block=16, blocks_per_sm=1), dict(order=gpm.GPM_ORDER_ID),
+    dict(warps_per_block=1, blocks_per_sm=1)])
+def test_schedule_never_changes_counts(cfg):
+    g = G.sbm(600, 60, 0.4, 0.02, 5)
+    dg = gpm.graph_from_csr(g)
+    ref_c = [O.clique_count(g, k) for k in (4, 6)]
+    ref_m = O.motif_count(g, 4)
+    gpm.gpm_set_config(dg, **cfg)
+    assert [gpm.gpm_clique_count(dg, k) for k in (4, 6)] == ref_c
+    assert motif_by_code(dg, 4) == ref_m
+
+
+# --------------------------------------------------------- invalid inputs
+
+@pytest.mark.parametrize("bad", ["unsorted", "asymmetric", "selfloop", "duplicate", "range"])
+def test_invalid_csr_rejected(bad):
+    ip = np.array([0, 2, 4, 6], dtype=np.int32)
+    ix = np.array([1, 2, 0, 2, 0, 1], dtype=np.int32)   # triangle
+    if bad == "unsorted":
+        ix = np.array([2, 1, 0, 2, 0, 1], dtype=np.int32)
+    elif bad == "asymmetric":
+        ix = np.array([1, 2, 0, 2, 1, 1], dtype=np.int32)
+    elif bad == "selfloop":
+        ix = np.array([0, 1, 0, 2, 0, 1], dtype=np.int32)
+    elif bad == "duplicate":
+        ix = np.array([1, 1, 0, 2, 0, 1], dtype=np.int32)
+    elif bad == "range":
+        ix = np.array([1, 7, 0, 2, 0, 1], dtype=np.int32)
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.gpm_graph_create(ip, ix, 3)
+    assert e.value.status == gpm.GPM_EINVAL
+    gpm.gpm_graph_create(ip, ix, 3, flags=gpm.GPM_SKIP_VALIDATE).close()
+
+
+def test_bounded_wait_times_out_and_recovers():
+    """One heavy root and donation off: every other warp is idle while
+    nothing completes, so with a 1 ms idle limit the wait runs out and the
+    call returns GPM_ETIMEOUT (the busy warp sees the flag and stops); the
+    same graph then counts correctly with the default limit."""
+    g = G.complete(140)
+    dg = gpm.graph_from_csr(g)
+    root = np.array([0], dtype=np.int32)
+    gpm.gpm_set_config(dg, donate=0, max_idle_ms=1)
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, 7, root)
+    assert e.value.status == gpm.GPM_ETIMEOUT
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, 5, root)
+    assert e.value.status == gpm.GPM_ETIMEOUT
+    gpm.gpm_set_config(dg, donate=1, max_idle_ms=120000)
+    assert gpm.gpm_clique_count(dg, 5) == comb(140, 5)
+    got = gpm.gpm_motif_count(dg, 4)
+    assert int(got.sum()) == comb(140, 4) and int(got[-1]) == comb(140, 4)
+
+
+# ------------------------------------------------ stored workload values
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{name}.json not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", ["er516", "sbm2000"])
+def test_workload_golden(name):
+    data = _golden(name)
+    g = G.workload(name)
+    assert g.sha256() == data["sha256"]
+    dg = gpm.graph_from_csr(g)
+    for case in data["cases"]:
+        k = case["k"]
+        roots = case["roots"]
+        if case["app"] == "clique":
+            if roots is None:
+                assert gpm.gpm_clique_count(dg, k) == case["total"], case["k"]
+            else:
+                c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, k, roots, per_root=True)
+                assert int(c[0]) == case["total"]
+                assert [int(x) for x in pr] == case["per_root"]
+        else:
+            want = {int(c): v for c, v in case["patterns"].items()}
+            if roots is None:
+                assert motif_by_code(dg, k) == want
+            else:
+                c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, k, roots, per_root=True)
+                got = {gpm.gpm_motif_pattern(k, p): int(x) for p, x in enumerate(c) if x}
+                assert got == want
+                assert [int(x) for x in pr] == case["per_root"]
