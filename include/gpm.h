@@ -181,6 +181,67 @@ typedef struct {
 
 gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
 
+/* ------------------------------------------------------------------------
+ * Learned scheduler (not in the paper; changes only the order and splitting
+ * of work, never a count).  A small MLP (8 -> 64 -> 64 -> 1, ReLU, BF16
+ * weights, FP32 accumulation) predicts each root's enumeration-subtree size
+ * from 8 per-root features; roots are then run heaviest-predicted first and
+ * the heaviest are pre-split into several work units.
+ * ---------------------------------------------------------------------- */
+
+#define GPM_MLP_PARAMS 4801   /* W1 64x8, b1 64, W2 64x64, b2 64, w3 64, b3 1 (row-major, this order) */
+
+/*
+ * Per-vertex features, FP32 [n][8]: log1p of degree, of oriented out-degree,
+ * of the number of higher-id neighbours, of the neighbour-degree sum, of the
+ * higher-id neighbour-degree sum, of the triangles rooted at v (lowest
+ * (degree, id) vertex), of the largest neighbour degree; and v / n.
+ * out: n*8 floats, a device pointer if flags has GPM_DEVICE_PTRS, else host.
+ */
+gpm_status gpm_root_features(gpm_graph* g, float* out, uint32_t flags);
+
+/*
+ * y[i] = MLP(x[i]) for i < n.  w_bf16: GPM_MLP_PARAMS BF16 values (as
+ * uint16); x: n*8 FP32; y: n FP32.  All device pointers; stream: cudaStream_t
+ * (NULL = legacy default).  Asynchronous on the stream.
+ */
+gpm_status gpm_mlp_forward(const uint16_t* w_bf16, const float* x, int64_t n, float* y, void* stream);
+
+/*
+ * grad[GPM_MLP_PARAMS] = gradient of mean_i (MLP(x[i]) - t[i])^2 with respect
+ * to the (BF16) parameters, and loss[0] = that mean.  Device pointers,
+ * overwritten; asynchronous on the stream.
+ */
+gpm_status gpm_mlp_grad(const uint16_t* w_bf16, const float* x, const float* t, int64_t n, float* grad,
+                        float* loss, void* stream);
+
+/*
+ * One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step >= 1)
+ * on FP32 master weights with FP32 moments m, v, then w_bf16 = BF16(master)
+ * rounded to nearest-even.  Device pointers; asynchronous on the stream.
+ */
+gpm_status gpm_mlp_adam(float* master, float* m, float* v, const float* grad, int32_t step, float lr,
+                        uint16_t* w_bf16, void* stream);
+
+/*
+ * Build the schedule of app over a root set: roots (host, n_roots distinct
+ * vertex ids; NULL = every vertex) are ordered by score descending (scores:
+ * device pointer to one FP32 per VERTEX; NULL = the plain order: degree for
+ * motifs, oriented out-degree for cliques), and the first split_roots of that
+ * order are each pre-split into split_chunks units over equal ranges of their
+ * children.  Replaces any earlier schedule of that app.
+ */
+gpm_status gpm_sched_from_scores(gpm_graph* g, int app, const float* scores, const int32_t* roots,
+                                 int64_t n_roots, int32_t split_roots, int32_t split_chunks);
+
+/*
+ * Exact counts over the scheduled root set of app (as gpm_count_roots, but
+ * run in the schedule's order and splitting).  per_root (nullable) is indexed
+ * like the roots array given to gpm_sched_from_scores.
+ */
+gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, int64_t counts_len,
+                               uint64_t* per_root);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* gpm_last_error(void);
 

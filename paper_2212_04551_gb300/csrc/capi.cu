@@ -228,6 +228,154 @@ gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out) {
     });
 }
 
+gpm_status gpm_root_features(gpm_graph* g, float* out, uint32_t flags) {
+    return guarded([&] {
+        check_graph(g);
+        if (!out) fail(GPM_EINVAL, "out is NULL");
+        if (flags & GPM_DEVICE_PTRS) {
+            root_features(g, out);
+        } else {
+            DevBuf tmp;
+            tmp.ensure(sizeof(float) * 8 * std::max(g->n, 1));
+            root_features(g, tmp.as<float>());
+            GPM_CUDA(cudaMemcpyAsync(out, tmp.ptr, sizeof(float) * 8 * g->n, cudaMemcpyDeviceToHost, g->stream));
+            GPM_CUDA(cudaStreamSynchronize(g->stream));
+        }
+    });
+}
+
+gpm_status gpm_mlp_forward(const uint16_t* w_bf16, const float* x, int64_t n, float* y, void* stream) {
+    return guarded([&] {
+        if (n < 0) fail(GPM_EINVAL, "n < 0");
+        if (n > 0 && (!w_bf16 || !x || !y)) fail(GPM_EINVAL, "NULL pointer");
+        mlp_forward(w_bf16, x, n, y, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+gpm_status gpm_mlp_grad(const uint16_t* w_bf16, const float* x, const float* t, int64_t n, float* grad,
+                        float* loss, void* stream) {
+    return guarded([&] {
+        if (n < 0) fail(GPM_EINVAL, "n < 0");
+        if (!w_bf16 || !grad || !loss || (n > 0 && (!x || !t))) fail(GPM_EINVAL, "NULL pointer");
+        mlp_grad(w_bf16, x, t, n, grad, loss, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+gpm_status gpm_mlp_adam(float* master, float* m, float* v, const float* grad, int32_t step, float lr,
+                        uint16_t* w_bf16, void* stream) {
+    return guarded([&] {
+        if (!master || !m || !v || !grad || !w_bf16) fail(GPM_EINVAL, "NULL pointer");
+        if (step < 1) fail(GPM_EINVAL, "step must be >= 1");
+        mlp_adam(master, m, v, grad, step, lr, w_bf16, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+gpm_status gpm_sched_from_scores(gpm_graph* g, int app, const float* scores, const int32_t* roots,
+                                 int64_t n_roots, int32_t split_roots, int32_t split_chunks) {
+    return guarded([&] {
+        check_graph(g);
+        if (app != GPM_APP_CLIQUE && app != GPM_APP_MOTIF) fail(GPM_EINVAL, "unknown app");
+        if (split_roots < 0 || split_chunks < 0) fail(GPM_EINVAL, "negative split");
+        const int64_t nr = roots ? n_roots : g->n;
+        if (nr < 0) fail(GPM_EINVAL, "n_roots < 0");
+        // the caller's list (validated: ids in range, each once)
+        std::vector<int32_t> list(nr);
+        if (roots) {
+            std::vector<uint8_t> seen(g->n, 0);
+            for (int64_t i = 0; i < nr; i++) {
+                const int32_t r = roots[i];
+                if (r < 0 || r >= g->n) fail(GPM_EINVAL, "root id out of range");
+                if (seen[r]) fail(GPM_EINVAL, "root listed twice");
+                seen[r] = 1;
+                list[i] = r;
+            }
+        } else {
+            for (int64_t i = 0; i < nr; i++) list[i] = (int32_t)i;
+        }
+        DevBuf d_list, d_key;
+        d_list.ensure(sizeof(int32_t) * std::max<int64_t>(nr, 1));
+        if (nr > 0)
+            GPM_CUDA(cudaMemcpyAsync(d_list.ptr, list.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, g->stream));
+        const float* key = scores;
+        if (!key) {
+            // plain order: degree (motif) or oriented out-degree (clique) as the score
+            if (app == GPM_APP_CLIQUE) ensure_dag(g);
+            std::vector<int32_t> dh(g->n);
+            const DevBuf& src = app == GPM_APP_CLIQUE ? g->dag_outdeg : g->degree;
+            if (g->n > 0)
+                GPM_CUDA(cudaMemcpyAsync(dh.data(), src.ptr, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, g->stream));
+            GPM_CUDA(cudaStreamSynchronize(g->stream));
+            std::vector<float> fh(g->n);
+            for (int32_t v = 0; v < g->n; v++) fh[v] = (float)dh[v];
+            d_key.ensure(sizeof(float) * std::max(g->n, 1));
+            if (g->n > 0)
+                GPM_CUDA(cudaMemcpyAsync(d_key.ptr, fh.data(), sizeof(float) * g->n, cudaMemcpyHostToDevice, g->stream));
+            key = d_key.as<float>();
+        }
+        auto& S = g->sched[app];
+        S.ready = false;
+        order_by_score(g, key, d_list.as<int32_t>(), nr, S.roots);
+        // the kernel takes the split roots from the END of its list: rotate the
+        // top split_roots to the back (their relative order kept)
+        std::vector<int32_t> ord(nr);
+        if (nr > 0)
+            GPM_CUDA(cudaMemcpyAsync(ord.data(), S.roots.ptr, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, g->stream));
+        GPM_CUDA(cudaStreamSynchronize(g->stream));
+        const int64_t ns = split_chunks > 1 ? std::min<int64_t>(split_roots, nr) : 0;
+        std::vector<int32_t> kern;
+        kern.reserve(nr);
+        for (int64_t i = ns; i < nr; i++) kern.push_back(ord[i]);
+        for (int64_t i = 0; i < ns; i++) kern.push_back(ord[i]);
+        std::vector<int64_t> where(g->n, -1);
+        for (int64_t i = 0; i < nr; i++) where[list[i]] = i;
+        S.caller_index.assign(nr, 0);
+        for (int64_t i = 0; i < nr; i++) S.caller_index[i] = where[kern[i]];
+        if (nr > 0)
+            GPM_CUDA(cudaMemcpyAsync(S.roots.ptr, kern.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, g->stream));
+        GPM_CUDA(cudaStreamSynchronize(g->stream));
+        S.n = nr;
+        S.n_counter = nr - ns;
+        S.chunks = ns > 0 ? split_chunks : 0;
+        S.ready = true;
+    });
+}
+
+gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, int64_t counts_len,
+                               uint64_t* per_root) {
+    return guarded([&] {
+        check_graph(g);
+        if (!counts) fail(GPM_EINVAL, "counts is NULL");
+        if (app != GPM_APP_CLIQUE && app != GPM_APP_MOTIF) fail(GPM_EINVAL, "unknown app");
+        auto& S = g->sched[app];
+        if (!S.ready) fail(GPM_EINVAL, "no schedule set for this app (gpm_sched_from_scores)");
+        unsigned long long* d_pr = nullptr;
+        if (per_root) {
+            g->per_root_tmp.ensure(sizeof(unsigned long long) * std::max<int64_t>(S.n, 1));
+            d_pr = g->per_root_tmp.as<unsigned long long>();
+        }
+        std::vector<uint64_t> c;
+        if (app == GPM_APP_CLIQUE) {
+            if (k < 1 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "k out of range [1, 16]");
+            if (counts_len < 1) fail(GPM_EINVAL, "counts_len < 1");
+            c.assign(1, 0);
+            run_clique(g, k, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, S.chunks);
+        } else {
+            if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+            const PatternTable& t = pattern_table(k);
+            if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
+            c.assign(t.num_patterns, 0);
+            run_motif(g, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, S.chunks);
+        }
+        if (per_root && S.n > 0) {
+            std::vector<uint64_t> tmp(S.n);
+            GPM_CUDA(cudaMemcpyAsync(tmp.data(), d_pr, sizeof(uint64_t) * S.n, cudaMemcpyDeviceToHost, g->stream));
+            GPM_CUDA(cudaStreamSynchronize(g->stream));
+            for (int64_t i = 0; i < S.n; i++) per_root[S.caller_index[i]] = tmp[i];
+        }
+        std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
+    });
+}
+
 const char* gpm_last_error(void) { return last_error_cstr(); }
 
 }  // extern "C"

@@ -167,6 +167,8 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
     int cached_root = -1;
     bool idle = false;
+    unsigned long long polls = 0;
+    int spin = 0;
     long long last_pending = -1;
     unsigned long long idle_since = 0;
     bool aborted = false;
@@ -182,7 +184,8 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
                 gpm_q_release(p.qseq, p.qcap, pos);
                 kind = 2;
             } else {
-                const unsigned long long r = atomicAdd(&ctl->next_root, 1ull);
+                unsigned long long r = *(volatile unsigned long long*)&ctl->next_root;
+                if (r < (unsigned long long)p.n_roots) r = atomicAdd(&ctl->next_root, 1ull);
                 if (r < (unsigned long long)p.n_roots) {
                     unit->root_pos = (int32_t)r;
                     unit->depth = 0;
@@ -220,14 +223,15 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
                 if (lane == 0) atomicCAS(&ctl->error, 0, DEV_ETIMEOUT);
                 break;
             }
-            if (lane == 0) atomicAdd(&ctl->idle_polls, 1ull);
-            __nanosleep(2000);
+            polls++;
+            __nanosleep(++spin < 32 ? 256 : 2048);   // short backoff first, then longer
             continue;
         }
         if (idle) {
             if (lane == 0) atomicSub(&ctl->idle, 1);
             idle = false;
         }
+        spin = 0;
 
         // ---- process the unit
         const int root_pos = unit->root_pos;
@@ -395,8 +399,31 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     const unsigned long long tot = gpm_warp_sum(top_sum);
     __syncwarp();
     if (lane == 0) {
+        if (polls) atomicAdd(&ctl->idle_polls, polls);
         add_count(ctl, p.k_hi, tot);
         for (int j = p.k_lo; j < p.k_hi; j++) add_count(ctl, j, wcnt[j]);
+    }
+}
+
+// Pre-split seeds: split root j (entries [n_counter, n_counter + n_split) of
+// the root list) into `chunks` units over equal index ranges of its children,
+// placed in queue slots [j*chunks, (j+1)*chunks) and published.
+__global__ void k_clique_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
+                              const int32_t* __restrict__ outdeg, QSeq* qseq, CliqueUnit* qunits) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_split) return;
+    const long long pos = n_counter + j;
+    const int d = outdeg[roots[pos]];
+    for (int c = 0; c < chunks; c++) {
+        const long long slot = (long long)j * chunks + c;
+        CliqueUnit u;
+        u.root_pos = (int32_t)pos;
+        u.depth = 0;
+        u.lo = (int)((long long)d * c / chunks);
+        u.hi = (int)((long long)d * (c + 1) / chunks);
+        for (int z = 0; z < GPM_CLIQUE_MAX_K; z++) u.path[z] = 0;
+        qunits[slot] = u;
+        qseq[slot].seq = (unsigned long long)slot + 1;
     }
 }
 
@@ -416,18 +443,25 @@ __global__ void k_clique_small(const int32_t* __restrict__ outdeg, const int32_t
 }
 
 void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
-                unsigned long long* d_per_root, uint64_t* counts_out) {
+                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, int split_chunks) {
     if (k_lo < 1 || k_hi > GPM_CLIQUE_MAX_K || k_lo > k_hi) fail(GPM_EINVAL, "bad clique size range");
     ensure_dag(g);
     cudaStream_t s = g->stream;
     if (!d_roots) {
         d_roots = ensure_root_order(g, GPM_APP_CLIQUE);
         n_roots = g->n;
+        n_counter = -1;
     }
+    if (n_counter < 0 || n_counter > n_roots) n_counter = n_roots;
+    const int n_split = (int)(n_roots - n_counter);
+    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > CQ_QUEUE_CAP / 2))
+        fail(GPM_EINVAL, "pre-split schedule does not fit the work queue");
+    const unsigned long long n_seed = n_split > 0 ? (unsigned long long)n_split * split_chunks : 0ull;
     g->scratch_small.ensure(sizeof(Control));
     Control* ctl = g->scratch_small.as<Control>();
     Control h{};
-    h.pending = n_roots;
+    h.pending = n_counter + (long long)n_seed;
+    h.q_tail = n_seed;
     GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
     if (d_per_root && n_roots > 0)
         GPM_CUDA(cudaMemsetAsync(d_per_root, 0, sizeof(unsigned long long) * n_roots, s));
@@ -450,7 +484,7 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         p.adj = g->dag_adj.as<int32_t>();
         p.outdeg = g->dag_outdeg.as<int32_t>();
         p.roots = d_roots;
-        p.n_roots = n_roots;
+        p.n_roots = n_counter;
         p.k_lo = std::max(k_lo, 3);
         p.k_hi = k_hi;
         p.maxd = std::max(g->max_outdeg, 1);
@@ -472,6 +506,9 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         p.qunits = reinterpret_cast<CliqueUnit*>(p.qseq + CQ_QUEUE_CAP);
         p.qcap = CQ_QUEUE_CAP;
         k_queue_init<<<16, 256, 0, s>>>(p.qseq, CQ_QUEUE_CAP);
+        if (n_split > 0)
+            k_clique_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks,
+                                                               p.outdeg, p.qseq, p.qunits);
         p.ctl = ctl;
         p.per_root = d_per_root;
         p.donate = g->cfg.donate;

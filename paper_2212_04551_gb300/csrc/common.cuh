@@ -89,6 +89,15 @@ struct gpm_graph {
     gpm::DevBuf roots_tmp;         // caller root lists
     gpm::DevBuf per_root_tmp;
 
+    // schedules built by gpm_sched_from_scores, per application
+    struct Sched {
+        bool ready = false;
+        gpm::DevBuf roots;                 // kernel order: counter roots, then split roots
+        int64_t n = 0, n_counter = 0;
+        int32_t chunks = 0;
+        std::vector<int64_t> caller_index; // kernel position -> index in the caller's list
+    } sched[2];
+
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     gpm_config cfg{};
     gpm_stats stats{};
@@ -140,10 +149,22 @@ const PatternTable& pattern_table(int k);  // built once per k, cached
 const uint16_t* device_lut(int k);         // uploaded once per (device, k)
 
 // clique.cu / motif.cu
+// d_roots[0 .. n_roots): the roots; the first n_counter are handed out one by
+// one, the rest are pre-split into split_chunks queue units each (n_counter
+// < 0: no pre-split).  d_roots == NULL: every vertex, heaviest first.
 void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
-                unsigned long long* d_per_root, uint64_t* counts_out);
+                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
+                int split_chunks = 0);
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
-               unsigned long long* d_per_root, uint64_t* counts_out);
+               unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
+               int split_chunks = 0);
+
+// sched.cu
+void root_features(gpm_graph* g, float* d_out);
+void mlp_forward(const uint16_t* w, const float* x, int64_t n, float* y, cudaStream_t s);
+void mlp_grad(const uint16_t* w, const float* x, const float* t, int64_t n, float* grad, float* loss, cudaStream_t s);
+void mlp_adam(float* master, float* m, float* v, const float* grad, int step, float lr, uint16_t* w, cudaStream_t s);
+void order_by_score(gpm_graph* g, const float* d_score, const int32_t* d_roots, int64_t n_roots, DevBuf& out);
 
 // helpers
 int resident_blocks(const void* kernel, int threads, size_t smem);

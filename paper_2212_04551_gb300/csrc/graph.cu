@@ -374,7 +374,7 @@ gpm_config default_config() {
     gpm_config c;
     c.warps_per_block = 8;
     c.blocks_per_sm = 0;
-    c.donate_min = 2;
+    c.donate_min = 4;
     c.order = GPM_ORDER_DEGREE_DESC;
     c.max_idle_ms = 120000;
     c.donate = 1;

@@ -51,7 +51,8 @@ struct MotifUnit {
     int32_t len;                // entries in the payload list (its extension array suffix)
     int32_t child_hi;           // children to expand: list positions [0, child_hi)
     int32_t sub[MT_MAXK];
-    int32_t pad;
+    int32_t list_off;           // >= 0: the list is indices[list_off ..] (a root's own
+                                // extension set); < 0: it is the slot's payload
 };
 static_assert(sizeof(MotifUnit) % 4 == 0, "unit must be word-sized");
 
@@ -129,6 +130,8 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
     const int32_t* __restrict__ indices = p.indices;
 
     bool idle = false;
+    unsigned long long polls = 0;
+    int spin = 0;
     long long last_pending = -1;
     unsigned long long idle_since = 0;
     bool aborted = false;
@@ -142,7 +145,8 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                 kind = 2;
                 W->qpos = pos;
             } else {
-                const unsigned long long r = atomicAdd(&ctl->next_root, 1ull);
+                unsigned long long r = *(volatile unsigned long long*)&ctl->next_root;
+                if (r < (unsigned long long)p.n_roots) r = atomicAdd(&ctl->next_root, 1ull);
                 if (r < (unsigned long long)p.n_roots) {
                     W->unit.root_pos = (int32_t)r;
                     W->unit.depth = 1;
@@ -178,14 +182,15 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                 if (lane == 0) atomicCAS(&ctl->error, 0, DEV_ETIMEOUT);
                 break;
             }
-            if (lane == 0) atomicAdd(&ctl->idle_polls, 1ull);
-            __nanosleep(2000);
+            polls++;
+            __nanosleep(++spin < 32 ? 256 : 2048);   // short backoff first, then longer
             continue;
         }
         if (idle) {
             if (lane == 0) atomicSub(&ctl->idle, 1);
             idle = false;
         }
+        spin = 0;
 
         // ---------------------------------------------------- set up the unit
         const int root_pos = W->unit.root_pos;
@@ -223,6 +228,15 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                 W->len[1] = e - lo;
                 W->cur[1] = 0;
                 W->hi[1] = e - lo;
+            }
+        } else if (W->unit.list_off >= 0) {
+            // pre-split seed: the list is a suffix of the root's adjacency
+            unit_ext = indices + W->unit.list_off;
+            if (lane == 0) {
+                gpm_q_release(p.qseq, p.qcap, W->qpos);
+                W->len[pdepth] = W->unit.len;
+                W->cur[pdepth] = 0;
+                W->hi[pdepth] = W->unit.child_hi;
             }
         } else {
             int32_t* dst = slab + p.lvl_off[pdepth];
@@ -376,7 +390,7 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                             u.len = len - start;
                             u.child_hi = to - start;
                             for (int z = 0; z < MT_MAXK; z++) u.sub[z] = z < t ? W->sub[z] : -1;
-                            u.pad = 0;
+                            u.list_off = -1;
                             p.qunits[slot] = u;
                             W->hi[t] = start;
                             atomicAdd((unsigned long long*)&ctl->pending, 1ull);
@@ -414,6 +428,7 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
         }
     }
 
+    if (lane == 0 && polls) atomicAdd(&ctl->idle_polls, polls);
     __syncthreads();
     for (int j = threadIdx.x; j < p.npat; j += blockDim.x) {
         const unsigned long long v = bcnt[j];
@@ -424,8 +439,41 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
     }
 }
 
+// Pre-split seeds: root j of [n_counter, n_counter + n_split) is cut into
+// `chunks` units over equal index ranges of its first extension set
+// ({u in N(r): u > r}, a suffix of N(r)); each unit's list is that suffix from
+// its first child on, by reference into the adjacency array.
+__global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
+                             const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+                             QSeq* qseq, MotifUnit* qunits) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_split) return;
+    const long long pos = n_counter + j;
+    const int r = roots[pos];
+    const int b = indptr[r], e = indptr[r + 1];
+    int lo = b, hi = e;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (indices[mid] <= r) lo = mid + 1; else hi = mid;
+    }
+    const int L = e - lo;
+    for (int c = 0; c < chunks; c++) {
+        const long long slot = (long long)j * chunks + c;
+        const int a = (int)((long long)L * c / chunks), z = (int)((long long)L * (c + 1) / chunks);
+        MotifUnit u;
+        u.root_pos = (int32_t)pos;
+        u.depth = 1;
+        u.len = L - a;
+        u.child_hi = z - a;
+        for (int q = 0; q < MT_MAXK; q++) u.sub[q] = q == 0 ? r : -1;
+        u.list_off = lo + a;
+        qunits[slot] = u;
+        qseq[slot].seq = (unsigned long long)slot + 1;
+    }
+}
+
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
-               unsigned long long* d_per_root, uint64_t* counts_out) {
+               unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, int split_chunks) {
     if (k < 1 || k > MT_MAXK) fail(GPM_ENOTIMPL, "motif size k=" + std::to_string(k) + " not built");
     const PatternTable& tab = pattern_table(k);
     const int npat = (int)tab.num_patterns;
@@ -433,7 +481,13 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     if (!d_roots) {
         d_roots = ensure_root_order(g, GPM_APP_MOTIF);
         n_roots = g->n;
+        n_counter = -1;
     }
+    if (n_counter < 0 || n_counter > n_roots) n_counter = n_roots;
+    const int n_split = (int)(n_roots - n_counter);
+    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > MT_QUEUE_CAP / 2))
+        fail(GPM_EINVAL, "pre-split schedule does not fit the work queue");
+    const unsigned long long n_seed = n_split > 0 ? (unsigned long long)n_split * split_chunks : 0ull;
     gpm_stats st{};
     std::vector<unsigned long long> host(npat, 0);
 
@@ -481,7 +535,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.indptr = g->indptr.as<int32_t>();
     p.indices = g->indices.as<int32_t>();
     p.roots = d_roots;
-    p.n_roots = n_roots;
+    p.n_roots = n_counter;
     p.n = g->n;
     p.k = k;
     p.npat = npat;
@@ -512,7 +566,8 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     Control* ctl = g->scratch_small.as<Control>();
     p.counts = reinterpret_cast<unsigned long long*>(ctl + 1);
     Control h{};
-    h.pending = n_roots;
+    h.pending = n_counter + (long long)n_seed;
+    h.q_tail = n_seed;
     GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
     GPM_CUDA(cudaMemsetAsync(p.counts, 0, sizeof(unsigned long long) * MT_MAXPAT, s));
     if (d_per_root && n_roots > 0)
@@ -525,6 +580,9 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.qpayload = reinterpret_cast<int32_t*>(p.qunits + MT_QUEUE_CAP);
     p.qcap = MT_QUEUE_CAP;
     k_queue_init<<<16, 256, 0, s>>>(p.qseq, MT_QUEUE_CAP);
+    if (n_split > 0)
+        k_motif_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks, p.indptr,
+                                                          p.indices, p.qseq, p.qunits);
     p.ctl = ctl;
     p.per_root = d_per_root;
     p.donate = g->cfg.donate;

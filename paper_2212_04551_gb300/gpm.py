@@ -75,7 +75,15 @@ SIGNATURES = {
     "gpm_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
     "gpm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
     "gpm_last_error": (ctypes.c_char_p, []),
+    "gpm_root_features": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32]),
+    "gpm_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "gpm_mlp_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]),
+    "gpm_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp, _vp]),
+    "gpm_sched_from_scores": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i32p, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_int32]),
+    "gpm_count_scheduled": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int64, _u64p]),
 }
+GPM_MLP_PARAMS = 4801
 
 
 def library_path() -> str:
@@ -257,3 +265,70 @@ def gpm_last_error() -> str:
 def graph_from_csr(csr, stream=None, flags: int = 0) -> Graph:
     """Create a device graph from a ``graphs.CSR`` (host arrays)."""
     return gpm_graph_create(csr.indptr, csr.indices, csr.n, flags=flags, stream=stream)
+
+
+# ------------------------------------------------------- learned scheduler
+
+def _dev_ptr(t, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+def gpm_root_features(g: Graph, out=None):
+    """Per-vertex FP32 features [n][8]; into ``out`` (CUDA tensor) or a new host array."""
+    n = gpm_graph_info(g)[0]
+    if out is None:
+        arr = np.zeros((max(n, 1), 8), dtype=np.float32)
+        _check(load().gpm_root_features(g, arr.ctypes.data, 0), "gpm_root_features")
+        return arr[:n]
+    _check(load().gpm_root_features(g, _dev_ptr(out, "out"), GPM_DEVICE_PTRS), "gpm_root_features")
+    return out
+
+
+def gpm_mlp_forward(w_bf16, x, y, stream=None) -> None:
+    n = int(x.shape[0])
+    _check(load().gpm_mlp_forward(_dev_ptr(w_bf16, "w"), _dev_ptr(x, "x"), n, _dev_ptr(y, "y"),
+                                  _stream_handle(stream)), "gpm_mlp_forward")
+
+
+def gpm_mlp_grad(w_bf16, x, t, grad, loss, stream=None) -> None:
+    n = int(x.shape[0])
+    _check(load().gpm_mlp_grad(_dev_ptr(w_bf16, "w"), _dev_ptr(x, "x"), _dev_ptr(t, "t"), n,
+                               _dev_ptr(grad, "grad"), _dev_ptr(loss, "loss"), _stream_handle(stream)),
+           "gpm_mlp_grad")
+
+
+def gpm_mlp_adam(master, m, v, grad, step: int, lr: float, w_bf16, stream=None) -> None:
+    _check(load().gpm_mlp_adam(_dev_ptr(master, "master"), _dev_ptr(m, "m"), _dev_ptr(v, "v"),
+                               _dev_ptr(grad, "grad"), int(step), float(lr), _dev_ptr(w_bf16, "w"),
+                               _stream_handle(stream)), "gpm_mlp_adam")
+
+
+def gpm_sched_from_scores(g: Graph, app: int, scores=None, roots=None, split_roots: int = 0,
+                          split_chunks: int = 0) -> None:
+    sp = _dev_ptr(scores, "scores") if scores is not None else None
+    if roots is None:
+        rp, nr = None, 0
+    else:
+        r = np.ascontiguousarray(roots, dtype=np.int32)
+        rp, nr = r.ctypes.data_as(_i32p), int(r.shape[0])
+    _check(load().gpm_sched_from_scores(g, int(app), sp, rp, nr, int(split_roots), int(split_chunks)),
+           "gpm_sched_from_scores")
+
+
+def gpm_count_scheduled(g: Graph, app: int, k: int, n_roots: int | None = None, per_root: bool = False):
+    ncounts = 1 if app == GPM_APP_CLIQUE else gpm_motif_num_patterns(k)
+    counts = np.zeros(ncounts, dtype=np.uint64)
+    pr = None
+    if per_root:
+        if n_roots is None:
+            raise ValueError("per_root needs n_roots (the length of the scheduled root list)")
+        pr = np.zeros(max(n_roots, 1), dtype=np.uint64)
+    _check(load().gpm_count_scheduled(g, int(app), int(k), counts.ctypes.data_as(_u64p), ncounts,
+                                      pr.ctypes.data_as(_u64p) if pr is not None else None),
+           "gpm_count_scheduled")
+    return counts, (pr[:n_roots] if pr is not None else None)

@@ -60,30 +60,76 @@ def _motif_case(g, k, roots):
             "oracle_s": round(time.time() - t, 2)}
 
 
-def chunglu_roots(g):
-    """256 uniform roots plus 64 roots with oriented out-degree in [16, 64]."""
+def _dag_outdeg(g):
     d = g.degrees()
     e = g.edges()
     du, dv = d[e[:, 0]], d[e[:, 1]]
     fwd = (du < dv) | ((du == dv) & (e[:, 0] < e[:, 1]))
-    outdeg = np.bincount(np.where(fwd, e[:, 0], e[:, 1]), minlength=g.n)
-    a = G.sample_roots(g.n, 256, seed=11)
-    mid = (outdeg >= 16) & (outdeg <= 64)
+    return np.bincount(np.where(fwd, e[:, 0], e[:, 1]), minlength=g.n)
+
+
+def chunglu_roots(g):
+    """320 seeded roots the oracle can finish for k <= 8: 256 uniform roots
+    and 64 roots with oriented out-degree in [12, 24], all of degree <= 200
+    (the oracle's clique step scans the root's whole adjacency at every node,
+    and C(24, 7) bounds a root's 8-cliques)."""
+    d = g.degrees()
+    outdeg = _dag_outdeg(g)
+    ok = (d <= 200) & (outdeg <= 24)
+    a = G.sample_roots(g.n, 256, seed=11, exclude=~ok)
+    mid = ok & (outdeg >= 12)
     b = G.sample_roots(g.n, 64, seed=12, exclude=~mid)
     return np.unique(np.concatenate([a, b])).astype(np.int32)
 
 
+def bounded_roots(g, k, count, seed, min_id=0, max_reach=None):
+    """Seeded roots whose connected k-sets the oracle can enumerate: walking a
+    seeded permutation of the vertices >= min_id, a root r is kept when the
+    vertices > r within distance k-1 of r (restricted to vertices > r, the
+    only ones a set rooted at r can hold) number at most max_reach, so
+    C(reach, k-1) bounds its sets."""
+    from math import comb
+    if max_reach is None:
+        max_reach = {3: 2000, 4: 200, 5: 80, 6: 44, 7: 32}[k]
+    rng = np.random.default_rng(seed)
+    cand = rng.permutation(np.arange(min_id, g.n))
+    ip, ix = g.indptr, g.indices
+    out = []
+    for r in cand:
+        r = int(r)
+        seen = {r}
+        frontier = [r]
+        ok = True
+        for _ in range(k - 1):
+            nxt = []
+            for u in frontier:
+                for w in ix[ip[u]:ip[u + 1]]:
+                    w = int(w)
+                    if w > r and w not in seen:
+                        seen.add(w)
+                        nxt.append(w)
+                        if len(seen) - 1 > max_reach:
+                            ok = False
+                            break
+                if not ok:
+                    break
+            if not ok:
+                break
+            frontier = nxt
+        if ok and len(seen) > 1 and comb(len(seen) - 1, k - 1) > 0:
+            out.append(r)
+            if len(out) == count:
+                break
+    return np.sort(np.array(out, dtype=np.int32))
+
+
 def rmat_roots(g, k):
-    """1,024 seeded roots among vertices whose id is >= 1024 and degree <= 32
-    (R-MAT puts its hubs at small ids; every subgraph's root is its smallest
-    vertex, so these roots keep the hubs out of their subgraphs)."""
-    d = g.degrees()
-    ok = (np.arange(g.n) >= 1024) & (d <= 32)
-    return G.sample_roots(g.n, 1024, seed=20 + k, exclude=~ok)
+    """1,024 seeded bounded roots (see bounded_roots) among ids >= 1024."""
+    return bounded_roots(g, k, 1024, seed=20 + k, min_id=1024)
 
 
 def sbm_motif_roots(g):
-    return G.sample_roots(g.n, 64, seed=30)
+    return bounded_roots(g, 6, 32, seed=30, max_reach=400)
 
 
 def job(spec):

@@ -1,0 +1,161 @@
+"""The learned scheduler on the GPU: MLP kernels against the fp64 oracle, and
+schedules (plain, learned, adversarial, pre-split) that never change counts.
+
+Tolerances: the oracle evaluates the network in float64 on the identical BF16
+weights, so only the kernels' FP32 rounding differs.  A 64-term FP32 dot
+product with O(1) terms carries a relative error of a few 1e-6; the batch
+gradients sum up to 4,096 per-sample terms with atomics in arbitrary order
+(relative error <= ~n * 2^-24 ~ 2.4e-4 in the worst case).  The bars below
+(1e-4 for outputs, 2e-3 relative to the gradient's largest entry) sit above
+those bounds and far below what a wrong term, sign or index produces.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from oracle import oracle as O
+from paper_2212_04551_gb300 import gpm
+from paper_2212_04551_gb300 import graphs as G
+from paper_2212_04551_gb300 import learned as L
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    gpm.load()
+    return t
+
+
+def _weights(torch, seed):
+    master = L.init_master(seed)
+    rng = np.random.default_rng(seed)
+    master[512:576] = rng.normal(0, 0.1, 64).astype(np.float32)       # b1
+    master[4672:4736] = rng.normal(0, 0.1, 64).astype(np.float32)     # b2
+    master[4800] = 0.25                                               # b3
+    model = L.new_model(seed)
+    model.master.copy_(torch.from_numpy(master))
+    z = torch.zeros_like(model.master)
+    gpm.gpm_mlp_adam(model.master, torch.zeros_like(z), torch.zeros_like(z), z, 1, 0.0, model.w)
+    torch.cuda.synchronize()
+    wbits = model.w.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    wf = wbits.view(np.float32)
+    return model, wf
+
+
+def test_bf16_copy_matches_oracle_rounding(torch):
+    model, wf = _weights(torch, 3)
+    want = M.bf16_round(model.master.cpu().numpy())
+    assert np.array_equal(wf.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 1000, 4096])
+def test_forward_and_grad_vs_oracle(torch, n):
+    model, wf = _weights(torch, 5)
+    rng = np.random.default_rng(n)
+    X = rng.normal(0, 1.5, (n, 8)).astype(np.float32)
+    T = rng.normal(2, 3, n).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    y = L.predict(model, Xd).cpu().numpy()
+    p = M.unflatten(wf)
+    yo, cache = M.forward(p, X)
+    assert np.allclose(y, yo, rtol=1e-4, atol=1e-4)
+    grad = torch.zeros(gpm.GPM_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gpm.gpm_mlp_grad(model.w, Xd, Td, grad, loss)
+    g = grad.cpu().numpy()
+    go = np.concatenate([M.backward(cache, T)[k].ravel() for k in M.ORDER])
+    scale = np.abs(go).max()
+    assert np.abs(g - go).max() <= 2e-3 * scale
+    assert abs(float(loss.item()) - M.loss(yo, T)) <= 1e-4 * max(1.0, M.loss(yo, T))
+
+
+def test_adam_step_vs_oracle(torch):
+    model, wf = _weights(torch, 7)
+    rng = np.random.default_rng(1)
+    X = rng.normal(0, 1, (512, 8)).astype(np.float32)
+    T = rng.normal(0, 1, 512).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    master0 = model.master.cpu().numpy().astype(np.float64)
+    grad = torch.zeros(gpm.GPM_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gpm.gpm_mlp_grad(model.w, Xd, Td, grad, loss)
+    g = grad.cpu().numpy().astype(np.float64)
+    gpm.gpm_mlp_adam(model.master, model.m, model.v, grad, 1, 1e-2, model.w)
+    got = model.master.cpu().numpy()
+    zeros = {k: np.zeros(s) for k, s in M.SHAPES.items()}
+    nm, _, _ = M.adam_step(M.unflatten(master0), M.unflatten(g), zeros, zeros, 1, 1e-2)
+    want = M.flatten({k: v.astype(np.float32) for k, v in nm.items()})
+    assert np.allclose(got, want, rtol=1e-5, atol=1e-6)
+    wbits = model.w.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    assert np.array_equal(wbits, M.bf16_round(got).view(np.uint32))
+
+
+def test_training_reduces_loss_on_held_out_graphs(torch):
+    """Trained on 4 small R-MAT graphs, evaluated on 2 others: the held-out
+    MSE drops well below the untrained network's and below predicting the
+    training mean."""
+    X, T = L.training_set(gpm.GPM_APP_MOTIF, 4, seeds=range(200, 204), scale=9)
+    Xh, Th = L.training_set(gpm.GPM_APP_MOTIF, 4, seeds=range(300, 302), scale=9)
+    model = L.new_model(0)
+    before = L.mse(model, Xh, Th)
+    L.train(model, X, T, epochs=40, batch=512, lr=3e-3)
+    after = L.mse(model, Xh, Th)
+    const = float(((Th - T.mean()) ** 2).mean().item())
+    assert model.history[-1] < model.history[0]
+    assert after < 0.5 * before and after < 0.8 * const, (before, after, const)
+    pred = L.predict(model, Xh).cpu().numpy()
+    assert M.spearman(pred, Th.cpu().numpy()) > 0.5
+
+
+def test_features_match_definition(torch):
+    g = G.gnp(60, 0.15, 4)
+    dg = gpm.graph_from_csr(g)
+    f = gpm.gpm_root_features(dg)
+    d = g.degrees()
+    e = g.edges()
+    outdeg = np.zeros(g.n, dtype=np.int64)
+    for u, v in e:
+        a, b = (u, v) if (d[u], u) < (d[v], v) else (v, u)
+        outdeg[a] += 1
+    tri_root = np.zeros(g.n)
+    _, pr = O.clique_count(g, 3, order=O.ORDER_DEGREE, per_root=True)
+    tri_root[:] = pr
+    for v in range(g.n):
+        nb = g.indices[g.indptr[v]:g.indptr[v + 1]]
+        up = nb[nb > v]
+        want = [np.log1p(d[v]), np.log1p(outdeg[v]), np.log1p(len(up)), np.log1p(d[nb].sum()),
+                np.log1p(d[up].sum()), np.log1p(tri_root[v]), np.log1p(d[nb].max() if len(nb) else 0), v / g.n]
+        assert np.allclose(f[v], want, rtol=1e-5, atol=1e-6), v
+
+
+@pytest.mark.parametrize("app", [gpm.GPM_APP_CLIQUE, gpm.GPM_APP_MOTIF])
+def test_schedules_never_change_counts(torch, app):
+    g = G.rmat(11, 8, 0.57, 0.19, 0.19, 77)
+    dg = gpm.graph_from_csr(g)
+    k = 4
+    roots = G.sample_roots(g.n, 700, seed=3)
+    ref, ref_pr = gpm.gpm_count_roots(dg, app, k, roots, per_root=True)
+    X = L.features(dg, g.n)
+    model = L.new_model(1)
+    pred = L.predict(model, X)
+    rng = np.random.default_rng(0)
+    cases = [(None, 0, 0), (pred, 0, 0), (pred, 50, 8), (-pred, 100, 4), (pred, 6, 300),
+             (torch.from_numpy(rng.random(g.n).astype(np.float32)).cuda(), 60, 16)]
+    for scores, ns, ch in cases:
+        gpm.gpm_sched_from_scores(dg, app, scores, roots, ns, ch)
+        c, pr = gpm.gpm_count_scheduled(dg, app, k, n_roots=len(roots), per_root=True)
+        assert np.array_equal(c, ref), (ns, ch)
+        assert np.array_equal(pr, ref_pr), (ns, ch)
+    # the whole vertex set, pre-split heavy roots, against the oracle
+    gpm.gpm_sched_from_scores(dg, app, pred, None, 40, 16)
+    c, _ = gpm.gpm_count_scheduled(dg, app, 3)
+    if app == gpm.GPM_APP_CLIQUE:
+        assert int(c[0]) == O.clique_count(g, 3)
+    else:
+        got = {gpm.gpm_motif_pattern(3, p): int(x) for p, x in enumerate(c) if x}
+        assert got == O.motif_count(g, 3)
