@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpm", choices=["gpm", "reference"])
     ap.add_argument("--k-lo", type=int, default=4)
-    ap.add_argument("--k-hi", type=int, default=8)
+    ap.add_argument("--k-hi", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

@@ -160,6 +160,7 @@ typedef struct {
     int32_t max_idle_ms;       /* bounded wait: an idle warp gives up after this long  */
                                /* without any progress anywhere (GPM_ETIMEOUT)         */
     int32_t donate;            /* 0 disables work donation                             */
+    int32_t donate_after_us;   /* a unit is split only after it has run this long      */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */
@@ -241,6 +242,57 @@ gpm_status gpm_sched_from_scores(gpm_graph* g, int app, const float* scores, con
  */
 gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, int64_t counts_len,
                                uint64_t* per_root);
+
+/* ------------------------------------------------------------------------
+ * Batched persistent launch (not in the paper).  Many small graphs packed as
+ * one disjoint union are counted by ONE persistent kernel over (task, root)
+ * units, captured once in a CUDA graph and replayed on every call; results
+ * are per graph.
+ * ---------------------------------------------------------------------- */
+
+typedef struct gpm_batch gpm_batch; /* opaque, library-owned */
+
+/*
+ * graph_off: n_graphs+1 vertex offsets (graph g owns vertices graph_off[g] ..
+ * graph_off[g+1]-1); indptr / indices: the packed CSR over all
+ * graph_off[n_graphs] vertices with GLOBAL vertex ids (the conventions of
+ * gpm_graph_create; no edge may join two graphs -- checked unless
+ * GPM_SKIP_VALIDATE).  Host pointers unless flags has GPM_DEVICE_PTRS; all
+ * arrays are copied.  stream: cudaStream_t to run on (NULL: the library
+ * creates a private stream, because the legacy default stream cannot be
+ * captured).  Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA.
+ */
+gpm_status gpm_batch_create(const int32_t* graph_off, const int32_t* indptr, const int32_t* indices,
+                            int32_t n_graphs, uint32_t flags, void* stream, gpm_batch** out);
+
+/* Free a batch, its captured launches and device buffers.  NULL is allowed. */
+void gpm_batch_destroy(gpm_batch* b);
+
+/*
+ * Per-graph counts in one launch: clique_counts[g] = number of clique_k-
+ * cliques of graph g, motif_counts[g * P + p] = count of pattern p of size
+ * motif_k in graph g (P = gpm_motif_num_patterns(motif_k)).  A k of 0 skips
+ * that task (its array may then be NULL); otherwise 3 <= clique_k <= 16,
+ * 3 <= motif_k <= 7.  The first call with a given (clique_k, motif_k) and
+ * launch shape captures a CUDA graph; later calls replay it.
+ * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_EOVERFLOW, GPM_ENOTIMPL (a
+ * graph too large for the shared-memory state).
+ */
+gpm_status gpm_batch_count(gpm_batch* b, int clique_k, int motif_k, uint64_t* clique_counts, uint64_t* motif_counts);
+
+/*
+ * Autotune the launch shape for (clique_k, motif_k): warps per block {2, 4,
+ * 8, 16, 32} x resident blocks per SM {max, 1, 2} x unit order {tasks
+ * grouped, merged}, each timed as the median of `reps` replays; the fastest
+ * is kept for this batch (and cached in-process for batches of the same
+ * shape).  best (nullable) receives it; best_ms (nullable) its median time,
+ * or -1 when it came from the cache.
+ */
+gpm_status gpm_batch_autotune(gpm_batch* b, int clique_k, int motif_k, int reps, gpm_config* best,
+                              double* best_ms);
+
+gpm_status gpm_batch_set_config(gpm_batch* b, const gpm_config* cfg);
+gpm_status gpm_batch_get_stats(const gpm_batch* b, gpm_stats* out);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* gpm_last_error(void);

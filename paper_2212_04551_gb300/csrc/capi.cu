@@ -14,6 +14,13 @@
 #include "common.cuh"
 
 namespace gpm {
+gpm_batch* create_batch(const int32_t* graph_off, const int32_t* indptr, const int32_t* indices, int32_t n_graphs,
+                        uint32_t flags, void* stream);
+void destroy_batch(gpm_batch* b);
+void batch_count(gpm_batch* b, int kc, int km, uint64_t* clique_counts, uint64_t* motif_counts);
+gpm_config batch_autotune(gpm_batch* b, int kc, int km, int reps, double* best_ms);
+void batch_set_config(gpm_batch* b, const gpm_config& c);
+gpm_stats batch_stats(const gpm_batch* b);
 gpm_graph* create_graph(const int32_t* indptr, const int32_t* indices, int32_t n, uint32_t flags, void* stream);
 void destroy_graph(gpm_graph* g);
 const char* last_error_cstr();
@@ -216,6 +223,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.donate_min < 0) fail(GPM_EINVAL, "donate_min < 0");
         if (c.order < GPM_ORDER_ID || c.order > GPM_ORDER_CUSTOM) fail(GPM_EINVAL, "unknown order");
         if (c.max_idle_ms <= 0) fail(GPM_EINVAL, "max_idle_ms must be positive");
+        if (c.donate_after_us < 0) fail(GPM_EINVAL, "donate_after_us < 0");
         g->cfg = c;
     });
 }
@@ -373,6 +381,55 @@ gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, i
             for (int64_t i = 0; i < S.n; i++) per_root[S.caller_index[i]] = tmp[i];
         }
         std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
+    });
+}
+
+gpm_status gpm_batch_create(const int32_t* graph_off, const int32_t* indptr, const int32_t* indices,
+                            int32_t n_graphs, uint32_t flags, void* stream, gpm_batch** out) {
+    return guarded([&] {
+        if (!out) fail(GPM_EINVAL, "out is NULL");
+        *out = nullptr;
+        *out = create_batch(graph_off, indptr, indices, n_graphs, flags, stream);
+    });
+}
+
+void gpm_batch_destroy(gpm_batch* b) {
+    try {
+        destroy_batch(b);
+    } catch (...) {
+    }
+}
+
+gpm_status gpm_batch_count(gpm_batch* b, int clique_k, int motif_k, uint64_t* clique_counts, uint64_t* motif_counts) {
+    return guarded([&] {
+        if (!b) fail(GPM_EINVAL, "batch is NULL");
+        batch_count(b, clique_k, motif_k, clique_counts, motif_counts);
+    });
+}
+
+gpm_status gpm_batch_autotune(gpm_batch* b, int clique_k, int motif_k, int reps, gpm_config* best,
+                              double* best_ms) {
+    return guarded([&] {
+        if (!b) fail(GPM_EINVAL, "batch is NULL");
+        if (reps < 1) fail(GPM_EINVAL, "reps < 1");
+        double ms = 0;
+        const gpm_config c = batch_autotune(b, clique_k, motif_k, reps, &ms);
+        if (best) *best = c;
+        if (best_ms) *best_ms = ms;
+    });
+}
+
+gpm_status gpm_batch_set_config(gpm_batch* b, const gpm_config* cfg) {
+    return guarded([&] {
+        if (!b || !cfg) fail(GPM_EINVAL, "NULL argument");
+        batch_set_config(b, *cfg);
+    });
+}
+
+gpm_status gpm_batch_get_stats(const gpm_batch* b, gpm_stats* out) {
+    return guarded([&] {
+        if (!b || !out) fail(GPM_EINVAL, "NULL argument");
+        *out = batch_stats(b);
     });
 }
 

@@ -36,20 +36,9 @@
 #include <string>
 
 #include "common.cuh"
+#include "clique_dev.cuh"
 
 namespace gpm {
-
-constexpr int CQ_LEVELS = GPM_CLIQUE_MAX_K + 1;
-constexpr int CQ_MAX_OUTDEG = 1024;          // bitmap rows of at most 32 words
-constexpr unsigned long long CQ_QUEUE_CAP = 8192;
-
-struct CliqueUnit {
-    int32_t root_pos;                   // index into the root list
-    int32_t depth;                      // path length p: the node is a (p+1)-clique
-    int32_t lo, hi;                     // its children (local indices) in [lo, hi); hi < 0: all
-    uint16_t path[GPM_CLIQUE_MAX_K];    // local index chosen at sizes 1 .. p
-};
-static_assert(sizeof(CliqueUnit) % 4 == 0, "unit must be word-sized");
 
 struct CliqueParams {
     const int32_t* __restrict__ off;
@@ -68,83 +57,9 @@ struct CliqueParams {
     unsigned long long qcap;
     unsigned long long* per_root;   // nullable
     int donate, donate_min;
+    unsigned long long donate_after_ns;
     unsigned long long max_idle_ns;
 };
-
-// shared-memory layout of one warp, in 32-bit words
-struct CqLayout {
-    int wcnt, unit, cur, hi, cand, list, rows, total;
-};
-
-__host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, int ws) {
-    CqLayout L;
-    L.wcnt = 0;                                        // CQ_LEVELS x u64
-    L.unit = L.wcnt + 2 * CQ_LEVELS;                   // CliqueUnit
-    L.cur = L.unit + (int)(sizeof(CliqueUnit) / 4);
-    L.hi = L.cur + CQ_LEVELS;
-    L.cand = L.hi + CQ_LEVELS;                         // CQ_LEVELS x wmax candidate bitmaps
-    L.list = L.cand + CQ_LEVELS * wmax;                // 32*wmax ints: N+(r), later the child list
-    L.rows = L.list + 32 * wmax;                       // maxd x ws bit rows
-    L.total = L.rows + maxd * ws;
-    L.total = (L.total + 3) & ~3;                      // keep every warp 16-byte aligned
-    return L;
-}
-
-// bits [from, to) of 32-bit word q
-__device__ __forceinline__ uint32_t range_mask(int q, int from, int to) {
-    const int lo = max(from - 32 * q, 0);
-    const int hi = min(to - 32 * q, 32);
-    if (lo >= hi) return 0u;
-    const uint32_t upto = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
-    const uint32_t from_ = lo >= 32 ? 0u : ~((1u << lo) - 1u);
-    return upto & from_;
-}
-
-// smallest set bit of C in [from, to), or -1 (warp-uniform result; w <= 32)
-__device__ __forceinline__ int next_child(const uint32_t* C, int w, int from, int to, int lane) {
-    const uint32_t x = lane < w ? (C[lane] & range_mask(lane, from, to)) : 0u;
-    const unsigned b = __ballot_sync(GPM_FULL_MASK, x != 0);
-    if (!b) return -1;
-    const int q = __ffs(b) - 1;
-    const uint32_t wq = __shfl_sync(GPM_FULL_MASK, x, q);
-    return 32 * q + __ffs(wq) - 1;
-}
-
-__device__ __forceinline__ int count_range(const uint32_t* C, int w, int from, int to, int lane) {
-    const int c = lane < w ? __popc(C[lane] & range_mask(lane, from, to)) : 0;
-    return __reduce_add_sync(GPM_FULL_MASK, c);
-}
-
-__device__ __forceinline__ void add_count(Control* ctl, int j, unsigned long long v) {
-    if (!v) return;
-    const unsigned long long old = atomicAdd(&ctl->counts[j], v);
-    if (old + v < old) atomicExch(&ctl->overflow, 1);
-}
-
-// Build the root-local bit matrix: row i = N+(u_i) restricted to N+(r).
-__device__ void build_rows(const CliqueParams& p, int r, int d, int ws, int* list, uint32_t* rows,
-                           int lane) {
-    const int beg = p.off[r];
-    for (int t = lane; t < d; t += 32) list[t] = p.adj[beg + t];
-    for (int t = lane; t < d * ws; t += 32) rows[t] = 0u;
-    __syncwarp();
-    const int first = list[0], last = list[d - 1];
-    for (int i = 0; i < d; i++) {
-        const int u = list[i];
-        const int ub = p.off[u], du = p.outdeg[u];
-        for (int t = lane; t < du; t += 32) {
-            const int x = p.adj[ub + t];
-            if (x < first || x > last) continue;
-            int lo = 0, hi = d - 1;
-            while (lo < hi) {               // first index with list[idx] >= x
-                const int mid = (lo + hi) >> 1;
-                if (list[mid] < x) lo = mid + 1; else hi = mid;
-            }
-            if (list[lo] == x) atomicOr(&rows[i * ws + (lo >> 5)], 1u << (lo & 31));
-        }
-    }
-    __syncwarp();
-}
 
 __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -163,8 +78,28 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
 
     for (int j = lane; j < CQ_LEVELS; j += 32) wcnt[j] = 0ull;
     __syncwarp();
+    CliqueWalk walk;
+    walk.off = p.off;
+    walk.adj = p.adj;
+    walk.outdeg = p.outdeg;
+    walk.k_lo = p.k_lo;
+    walk.k_hi = p.k_hi;
+    walk.wmax = p.wmax;
+    walk.wcnt = wcnt;
+    walk.cur = cur;
+    walk.hiv = hiv;
+    walk.cand = cand;
+    walk.list = list;
+    walk.rows = rows;
+    walk.ctl = ctl;
+    walk.qseq = p.qseq;
+    walk.qunits = p.qunits;
+    walk.qcap = p.qcap;
+    walk.donate_min = p.donate_min;
+    walk.donate_after_ns = p.donate_after_ns;
 
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
+    unsigned long long top_km1 = 0;   // lane-private (k_hi-1)-clique count
     int cached_root = -1;
     bool idle = false;
     unsigned long long polls = 0;
@@ -237,153 +172,10 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
         const int root_pos = unit->root_pos;
         const int r = p.roots[root_pos];
         const int d = p.outdeg[r];
-        const int w = (d + 31) >> 5;
-        const int ws = w | 1;
         unsigned long long unit_sum = 0;   // lane-private k_hi-cliques of this unit
-        if (d >= p.k_lo - 1 && d > 0) {
-            if (r != cached_root) {
-                build_rows(p, r, d, ws, list, rows, lane);
-                cached_root = r;
-            }
-            // candidates of the unit's node: all of N+(r), then AND along the path
-            if (lane < w) cand[1 * p.wmax + lane] = range_mask(lane, 0, d);
-            __syncwarp();
-            const int depth = unit->depth;
-            int s = 1;
-            for (int t = 0; t < depth; t++) {
-                const int i = unit->path[t];
-                if (lane < w) cand[(s + 1) * p.wmax + lane] = cand[s * p.wmax + lane] & rows[i * ws + lane];
-                s++;
-                __syncwarp();
-            }
-            const int s_base = s;
-            if (lane == 0) {
-                cur[s] = unit->lo;
-                hiv[s] = unit->hi < 0 ? d : unit->hi;
-            }
-            __syncwarp();
-
-            int iter = 0;
-            for (;;) {
-                const uint32_t* Cs = cand + s * p.wmax;
-                if (s == p.k_hi - 2) {
-                    // last level: children of this node, lane-parallel
-                    const int from = cur[s], to = hiv[s];
-                    int nchild = 0;
-                    for (int q = 0; q < w; q++) {
-                        const uint32_t word = Cs[q] & range_mask(q, from, to);
-                        const bool bit = (word >> lane) & 1u;
-                        const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
-                        if (bit) list[nchild + __popc(bal & gpm_lanemask_lt())] = 32 * q + lane;
-                        nchild += __popc(bal);
-                    }
-                    __syncwarp();
-                    unsigned long long sum = 0;
-                    for (int t = lane; t < nchild; t += 32) {
-                        const uint32_t* row = rows + list[t] * ws;
-                        int c = 0;
-                        for (int q = 0; q < w; q++) c += __popc(Cs[q] & row[q]);
-                        sum += (unsigned)c;
-                    }
-                    unit_sum += sum;
-                    if (lane == 0 && s + 1 >= p.k_lo) wcnt[s + 1] += (unsigned)nchild;
-                    __syncwarp();
-                    if (s == s_base) break;
-                    s--;
-                    continue;
-                }
-                const int i = next_child(Cs, w, cur[s], hiv[s], lane);
-                if (i < 0) {
-                    if (s == s_base) break;
-                    s--;
-                    continue;
-                }
-                uint32_t* Cn = cand + (s + 1) * p.wmax;
-                uint32_t x = 0;
-                if (lane < w) {
-                    x = Cs[lane] & rows[i * ws + lane];
-                    Cn[lane] = x;
-                }
-                const int c = __reduce_add_sync(GPM_FULL_MASK, (unsigned)__popc(x));
-                if (lane == 0) {
-                    cur[s] = i + 1;
-                    if (s + 1 >= p.k_lo) wcnt[s + 1] += 1ull;
-                }
-                // descend while the child can still reach a counted size
-                const bool down = (s + 1 <= p.k_hi - 2) && c > 0 && (s + 1 + c >= p.k_lo);
-                if (down && lane == 0) {
-                    cur[s + 1] = 0;
-                    hiv[s + 1] = d;
-                }
-                __syncwarp();
-                if (down) s++;
-
-                if ((++iter & 15) == 0) {
-                    // abort on a device error; donate when someone is idle
-                    int err = 0, want = 0;
-                    if (lane == 0) {
-                        err = *(volatile int*)&ctl->error;
-                        if (p.donate) {
-                            const int idl = *(volatile int*)&ctl->idle;
-                            const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
-                            const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
-                            want = idl > 0 && (long long)(qt - qh) < (long long)idl;
-                        }
-                    }
-                    err = __shfl_sync(GPM_FULL_MASK, err, 0);
-                    if (err) { aborted = true; break; }
-                    want = __shfl_sync(GPM_FULL_MASK, want, 0);
-                    if (want) {
-                        // shallowest level (up to the current one) with enough siblings left
-                        for (int t = s_base; t <= s && t <= p.k_hi - 3; t++) {
-                            const uint32_t* Ct = cand + t * p.wmax;
-                            const int from = cur[t], to = hiv[t];
-                            const int rem = count_range(Ct, w, from, to, lane);
-                            if (rem < max(p.donate_min, 2)) continue;
-                            // keep the first rem - rem/2 remaining children, donate the rest
-                            const int keep = rem - rem / 2;
-                            int seen = 0, mid = -1;
-                            for (int q = 0; q < w && mid < 0; q++) {
-                                const uint32_t word = Ct[q] & range_mask(q, from, to);
-                                const int pc = __popc(word);
-                                if (seen + pc > keep) {
-                                    uint32_t wv = word;
-                                    for (int z = 0; z < keep - seen; z++) wv &= wv - 1u;
-                                    mid = 32 * q + __ffs(wv) - 1;
-                                }
-                                seen += pc;
-                            }
-                            if (mid < 0) break;
-                            int ok = 0;
-                            if (lane == 0) {
-                                unsigned long long pos;
-                                if (gpm_q_reserve(p.qseq, p.qcap, &ctl->q_tail, &pos)) {
-                                    CliqueUnit* dst = &p.qunits[pos % p.qcap];
-                                    CliqueUnit u;
-                                    u.root_pos = root_pos;
-                                    u.depth = depth + (t - s_base);
-                                    u.lo = mid;
-                                    u.hi = to;
-                                    for (int z = 0; z < depth; z++) u.path[z] = unit->path[z];
-                                    for (int z = s_base; z < t; z++) u.path[depth + (z - s_base)] = (uint16_t)(cur[z] - 1);
-                                    for (int z = u.depth; z < GPM_CLIQUE_MAX_K; z++) u.path[z] = 0;
-                                    *dst = u;
-                                    atomicAdd((unsigned long long*)&ctl->pending, 1ull);
-                                    __threadfence();
-                                    gpm_q_publish(p.qseq, p.qcap, pos);
-                                    atomicAdd(&ctl->donations, 1ull);
-                                    hiv[t] = mid;
-                                    ok = 1;
-                                }
-                            }
-                            ok = __shfl_sync(GPM_FULL_MASK, ok, 0);
-                            __syncwarp();
-                            break;
-                        }
-                    }
-                }
-            }
-        }
+        const bool ok = p.donate ? cq_walk<true>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, lane)
+                                 : cq_walk<false>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, lane);
+        if (!ok) aborted = true;
         top_sum += unit_sum;
         if (p.per_root) {
             const unsigned long long tot = gpm_warp_sum(unit_sum);
@@ -397,11 +189,13 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     }
 
     const unsigned long long tot = gpm_warp_sum(top_sum);
+    const unsigned long long km1 = gpm_warp_sum(top_km1);
     __syncwarp();
     if (lane == 0) {
         if (polls) atomicAdd(&ctl->idle_polls, polls);
         add_count(ctl, p.k_hi, tot);
-        for (int j = p.k_lo; j < p.k_hi; j++) add_count(ctl, j, wcnt[j]);
+        if (p.k_hi >= 4 && p.k_hi - 1 >= p.k_lo) add_count(ctl, p.k_hi - 1, km1);
+        for (int j = p.k_lo; j < p.k_hi - 1; j++) add_count(ctl, j, wcnt[j]);
     }
 }
 
@@ -513,6 +307,7 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         p.per_root = d_per_root;
         p.donate = g->cfg.donate;
         p.donate_min = std::max(2, g->cfg.donate_min);
+        p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
         p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
         GPM_CUDA(cudaEventRecord(g->ev0, s));
         k_clique<<<gr.blocks, wpb * 32, smem, s>>>(p);

@@ -1,0 +1,390 @@
+// clique_dev.cuh -- device code of one clique work unit (root-local bitmap
+// DFS, aggregate_counter by popcount, optional work donation), shared by the
+// single-graph kernel (clique.cu) and the batched kernel (batch.cu).
+//
+// The paper's clique loop (Algorithm 4) extends a traversal from tr[0]'s
+// adjacency, keeps extensions after the last vertex ("lower") and adjacent to
+// every traversal vertex ("is_clique"), and at |tr| = k-1 adds the number of
+// valid extensions (aggregate_counter).  Here the search runs on the
+// degree-ordered orientation, and the candidate set of a traversal -- its
+// valid extensions after both filters -- is a bitmap over the root's
+// out-neighbourhood N+(r):
+//
+//   * row i of a d x d bit matrix in shared memory holds N+(u_i) restricted
+//     to N+(r) (u_i = i-th out-neighbour of r, d = |N+(r)|);
+//   * the root's candidates are all d bits; choosing child i gives C & row_i
+//     (both filters in one AND: row_i holds only vertices after u_i, the AND
+//     keeps those adjacent to every traversal vertex);
+//   * at a node of size k-2 the k-cliques below it number sum over i in C of
+//     popc(C & row_i): aggregate_counter on every (k-1)-vertex child at once.
+//
+// Upper levels are walked one child at a time (the DFS step of Section 4.2);
+// the last level is expanded lane-parallel over the compacted candidate list
+// (the BFS step, one candidate per lane).
+#pragma once
+
+#include "common.cuh"
+
+namespace gpm {
+
+
+constexpr int CQ_LEVELS = GPM_CLIQUE_MAX_K + 1;
+constexpr int CQ_MAX_OUTDEG = 1024;          // bitmap rows of at most 32 words
+constexpr unsigned long long CQ_QUEUE_CAP = 8192;
+
+struct CliqueUnit {
+    int32_t root_pos;                   // index into the root list
+    int32_t depth;                      // path length p: the node is a (p+1)-clique
+    int32_t lo, hi;                     // its children (local indices) in [lo, hi); hi < 0: all
+    uint16_t path[GPM_CLIQUE_MAX_K];    // local index chosen at sizes 1 .. p
+};
+static_assert(sizeof(CliqueUnit) % 4 == 0, "unit must be word-sized");
+
+
+
+// shared-memory layout of one warp, in 32-bit words
+struct CqLayout {
+    int wcnt, unit, cur, hi, cand, list, rows, total;
+};
+
+__host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, int ws) {
+    CqLayout L;
+    L.wcnt = 0;                                        // CQ_LEVELS x u64
+    L.unit = L.wcnt + 2 * CQ_LEVELS;                   // CliqueUnit
+    L.cur = L.unit + (int)(sizeof(CliqueUnit) / 4);
+    L.hi = L.cur + CQ_LEVELS;
+    L.cand = L.hi + CQ_LEVELS;                         // CQ_LEVELS x wmax candidate bitmaps
+    L.list = L.cand + CQ_LEVELS * wmax;                // 32*wmax ints: N+(r), later the child list
+    L.rows = L.list + 32 * wmax;                       // maxd x ws bit rows
+    L.total = L.rows + maxd * ws;
+    L.total = (L.total + 3) & ~3;                      // keep every warp 16-byte aligned
+    return L;
+}
+
+// bits [from, to) of 32-bit word q
+__device__ __forceinline__ uint32_t range_mask(int q, int from, int to) {
+    const int lo = max(from - 32 * q, 0);
+    const int hi = min(to - 32 * q, 32);
+    if (lo >= hi) return 0u;
+    const uint32_t upto = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    const uint32_t from_ = lo >= 32 ? 0u : ~((1u << lo) - 1u);
+    return upto & from_;
+}
+
+// smallest set bit of C in [from, to), or -1 (warp-uniform result; w <= 32)
+__device__ __forceinline__ int next_child(const uint32_t* C, int w, int from, int to, int lane) {
+    const uint32_t x = lane < w ? (C[lane] & range_mask(lane, from, to)) : 0u;
+    const unsigned b = __ballot_sync(GPM_FULL_MASK, x != 0);
+    if (!b) return -1;
+    const int q = __ffs(b) - 1;
+    const uint32_t wq = __shfl_sync(GPM_FULL_MASK, x, q);
+    return 32 * q + __ffs(wq) - 1;
+}
+
+__device__ __forceinline__ int count_range(const uint32_t* C, int w, int from, int to, int lane) {
+    const int c = lane < w ? __popc(C[lane] & range_mask(lane, from, to)) : 0;
+    return __reduce_add_sync(GPM_FULL_MASK, c);
+}
+
+__device__ __forceinline__ void add_count(Control* ctl, int j, unsigned long long v) {
+    if (!v) return;
+    const unsigned long long old = atomicAdd(&ctl->counts[j], v);
+    if (old + v < old) atomicExch(&ctl->overflow, 1);
+}
+
+// Build the root-local bit matrix: row i = N+(u_i) restricted to N+(r).
+__device__ __noinline__ static void build_rows(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const int32_t* __restrict__ outdeg, int r, int d, int ws, int* list, uint32_t* rows,
+                           int lane) {
+    const int beg = off[r];
+    for (int t = lane; t < d; t += 32) list[t] = adj[beg + t];
+    for (int t = lane; t < d * ws; t += 32) rows[t] = 0u;
+    __syncwarp();
+    const int first = list[0], last = list[d - 1];
+    for (int i = 0; i < d; i++) {
+        const int u = list[i];
+        const int ub = off[u], du = outdeg[u];
+        for (int t = lane; t < du; t += 32) {
+            const int x = adj[ub + t];
+            if (x < first || x > last) continue;
+            int lo = 0, hi = d - 1;
+            while (lo < hi) {               // first index with list[idx] >= x
+                const int mid = (lo + hi) >> 1;
+                if (list[mid] < x) lo = mid + 1; else hi = mid;
+            }
+            if (list[lo] == x) atomicOr(&rows[i * ws + (lo >> 5)], 1u << (lo & 31));
+        }
+    }
+    __syncwarp();
+}
+
+
+// Everything one warp needs to walk one unit.
+struct CliqueWalk {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ adj;
+    const int32_t* __restrict__ outdeg;
+    int k_lo, k_hi;
+    int wmax;
+    // this warp's shared memory
+    unsigned long long* wcnt;   // per clique size, counts of sizes < k_hi - 1
+    int* cur;
+    int* hiv;
+    uint32_t* cand;
+    int* list;
+    uint32_t* rows;
+    // donation (DONATE only)
+    Control* ctl;
+    QSeq* qseq;
+    CliqueUnit* qunits;
+    unsigned long long qcap;
+    int donate_min;
+    unsigned long long donate_after_ns;   // a unit splits only after running this long
+};
+
+// Compact the children of a node (set bits of C in [from, to)) into list[];
+// returns how many.  Warp-uniform.
+__device__ __forceinline__ int cq_compact(const uint32_t* C, int w, int from, int to, int* list, int lane) {
+    int n = 0;
+    for (int q = 0; q < w; q++) {
+        const uint32_t word = C[q] & range_mask(q, from, to);
+        const bool bit = (word >> lane) & 1u;
+        const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
+        if (bit) list[n + __popc(bal & gpm_lanemask_lt())] = 32 * q + lane;
+        n += __popc(bal);
+    }
+    __syncwarp();
+    return n;
+}
+
+// The last two levels below a node of size k-3 with candidates C, children
+// list[0..nchild): lane t takes children t, t+32, ...; for child i it forms
+// C_i = C & row_i in registers (|C_i| = its (k-1)-clique children, added to
+// km1) and, for every j in C_i, adds popc(C_i & row_j) -- the k-cliques
+// through (i, j), aggregate_counter on each (k-1)-clique.  W >= w words.
+template <int W>
+__device__ __forceinline__ void cq_tail2(const uint32_t* C, const uint32_t* rows, int w, int ws, const int* list,
+                                         int nchild, unsigned long long& km1, unsigned long long& kk, int lane) {
+    uint32_t c[W];
+#pragma unroll
+    for (int q = 0; q < W; q++) c[q] = q < w ? C[q] : 0u;
+    for (int t = lane; t < nchild; t += 32) {
+        const uint32_t* ri = rows + list[t] * ws;
+        uint32_t ci[W];
+        int g = 0;
+#pragma unroll
+        for (int q = 0; q < W; q++) {
+            ci[q] = q < w ? (c[q] & ri[q]) : 0u;
+            g += __popc(ci[q]);
+        }
+        km1 += (unsigned)g;
+        unsigned acc = 0;
+        for (int q = 0; q < w; q++) {
+            // word q of C_i without dynamic register indexing
+            uint32_t bits = 0;
+#pragma unroll
+            for (int z = 0; z < W; z++)
+                if (z == q) bits = ci[z];
+            while (bits) {
+                const int j = 32 * q + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const uint32_t* rj = rows + j * ws;
+#pragma unroll
+                for (int z = 0; z < W; z++)
+                    if (z < w) acc += __popc(ci[z] & rj[z]);
+            }
+        }
+        kk += acc;
+    }
+}
+
+__device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint32_t* rows, int w, int ws,
+                                                  const int* list, int nchild, unsigned long long& km1,
+                                                  unsigned long long& kk, int lane) {
+    if (w <= 1) cq_tail2<1>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else if (w <= 2) cq_tail2<2>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else if (w <= 4) cq_tail2<4>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else if (w <= 6) cq_tail2<6>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else if (w <= 8) cq_tail2<8>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else if (w <= 10) cq_tail2<10>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else if (w <= 16) cq_tail2<16>(C, rows, w, ws, list, nchild, km1, kk, lane);
+    else {
+        // wide rows (out-degree > 512): C_i's words are recomputed from shared
+        // memory instead of held in registers
+        for (int t = lane; t < nchild; t += 32) {
+            const uint32_t* ri = rows + list[t] * ws;
+            unsigned long long acc = 0;
+            for (int q = 0; q < w; q++) {
+                uint32_t bits = C[q] & ri[q];
+                km1 += (unsigned)__popc(bits);
+                while (bits) {
+                    const int j = 32 * q + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const uint32_t* rj = rows + j * ws;
+                    for (int z = 0; z < w; z++) acc += __popc(C[z] & ri[z] & rj[z]);
+                }
+            }
+            kk += acc;
+        }
+    }
+}
+
+// Walk one unit (root r = roots[root_pos], d = |N+(r)|).  Returns false if it
+// stopped on a device error.  Lane-private results: unit_sum (k_hi-cliques)
+// and km1 (k_hi-1 cliques, used when k_lo < k_hi); smaller sizes go to wcnt.
+template <bool DONATE>
+__device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_pos, int r, int d, int& cached_root,
+                        unsigned long long& unit_sum, unsigned long long& km1, int lane) {
+    if (d < a.k_lo - 1 || d <= 0) return true;
+    const int w = (d + 31) >> 5;
+    const int ws = w | 1;
+    const int K = a.k_hi;
+    unsigned long long* wcnt = a.wcnt;
+    int* cur = a.cur;
+    int* hiv = a.hiv;
+    uint32_t* cand = a.cand;
+    int* list = a.list;
+    uint32_t* rows = a.rows;
+    if (r != cached_root) {
+        build_rows(a.off, a.adj, a.outdeg, r, d, ws, list, rows, lane);
+        cached_root = r;
+    }
+    // candidates of the unit's node: all of N+(r), then AND along the path
+    if (lane < w) cand[1 * a.wmax + lane] = range_mask(lane, 0, d);
+    __syncwarp();
+    const int depth = unit->depth;
+    int s = 1;
+    for (int t = 0; t < depth; t++) {
+        const int i = unit->path[t];
+        if (lane < w) cand[(s + 1) * a.wmax + lane] = cand[s * a.wmax + lane] & rows[i * ws + lane];
+        s++;
+        __syncwarp();
+    }
+    const int s_base = s;
+    if (lane == 0) {
+        cur[s] = unit->lo;
+        hiv[s] = unit->hi < 0 ? d : unit->hi;
+    }
+    __syncwarp();
+    // nodes of size `tail` are finished by the lane-parallel tail
+    const int tail = K >= 4 ? K - 3 : 1;
+    const unsigned long long t_start = DONATE ? gpm_globaltimer() : 0ull;
+
+    int iter = 0;
+    for (;;) {
+        const uint32_t* Cs = cand + s * a.wmax;
+        if (s == tail) {
+            const int nchild = cq_compact(Cs, w, cur[s], hiv[s], list, lane);
+            if (K == 3) {
+                // one level: 3-cliques = sum over children of popc(C & row_i)
+                unsigned long long sum = 0;
+                for (int t = lane; t < nchild; t += 32) {
+                    const uint32_t* row = rows + list[t] * ws;
+                    int c = 0;
+                    for (int q = 0; q < w; q++) c += __popc(Cs[q] & row[q]);
+                    sum += (unsigned)c;
+                }
+                unit_sum += sum;
+            } else {
+                if (lane == 0 && K - 2 >= a.k_lo) wcnt[K - 2] += (unsigned)nchild;
+                cq_tail2_dispatch(Cs, rows, w, ws, list, nchild, km1, unit_sum, lane);
+            }
+            __syncwarp();
+            if (s == s_base) break;
+            s--;
+            continue;
+        }
+        const int i = next_child(Cs, w, cur[s], hiv[s], lane);
+        if (i < 0) {
+            if (s == s_base) break;
+            s--;
+            continue;
+        }
+        uint32_t* Cn = cand + (s + 1) * a.wmax;
+        uint32_t x = 0;
+        if (lane < w) {
+            x = Cs[lane] & rows[i * ws + lane];
+            Cn[lane] = x;
+        }
+        const int c = __reduce_add_sync(GPM_FULL_MASK, (unsigned)__popc(x));
+        if (lane == 0) {
+            cur[s] = i + 1;
+            if (s + 1 >= a.k_lo) wcnt[s + 1] += 1ull;
+        }
+        // descend while the child can still reach a counted size
+        const bool down = c > 0 && (s + 1 + c >= a.k_lo);
+        if (down && lane == 0) {
+            cur[s + 1] = 0;
+            hiv[s + 1] = d;
+        }
+        __syncwarp();
+        if (down) s++;
+
+        if (DONATE && (++iter & 15) == 0) {
+            Control* ctl = a.ctl;
+            // abort on a device error; split when someone is idle and this
+            // unit has already run for a while
+            int err = 0, want = 0;
+            if (lane == 0) {
+                err = *(volatile int*)&ctl->error;
+                if (gpm_globaltimer() - t_start > a.donate_after_ns) {
+                    const int idl = *(volatile int*)&ctl->idle;
+                    const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
+                    const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
+                    want = idl > 0 && (long long)(qt - qh) < (long long)idl;
+                }
+            }
+            err = __shfl_sync(GPM_FULL_MASK, err, 0);
+            if (err) return false;
+            want = __shfl_sync(GPM_FULL_MASK, want, 0);
+            if (want) {
+                // shallowest level above the tail with enough siblings left
+                for (int t = s_base; t <= s && t < tail; t++) {
+                    const uint32_t* Ct = cand + t * a.wmax;
+                    const int from = cur[t], to = hiv[t];
+                    const int rem = count_range(Ct, w, from, to, lane);
+                    if (rem < max(a.donate_min, 2)) continue;
+                    // keep the first rem - rem/2 remaining children, donate the rest
+                    const int keep = rem - rem / 2;
+                    int seen = 0, mid = -1;
+                    for (int q = 0; q < w && mid < 0; q++) {
+                        const uint32_t word = Ct[q] & range_mask(q, from, to);
+                        const int pc = __popc(word);
+                        if (seen + pc > keep) {
+                            uint32_t wv = word;
+                            for (int z = 0; z < keep - seen; z++) wv &= wv - 1u;
+                            mid = 32 * q + __ffs(wv) - 1;
+                        }
+                        seen += pc;
+                    }
+                    if (mid < 0) break;
+                    if (lane == 0) {
+                        unsigned long long pos;
+                        if (gpm_q_reserve(a.qseq, a.qcap, &ctl->q_tail, &pos)) {
+                            CliqueUnit* dst = &a.qunits[pos % a.qcap];
+                            CliqueUnit u;
+                            u.root_pos = root_pos;
+                            u.depth = depth + (t - s_base);
+                            u.lo = mid;
+                            u.hi = to;
+                            for (int z = 0; z < depth; z++) u.path[z] = unit->path[z];
+                            for (int z = s_base; z < t; z++) u.path[depth + (z - s_base)] = (uint16_t)(cur[z] - 1);
+                            for (int z = u.depth; z < GPM_CLIQUE_MAX_K; z++) u.path[z] = 0;
+                            *dst = u;
+                            atomicAdd((unsigned long long*)&ctl->pending, 1ull);
+                            __threadfence();
+                            gpm_q_publish(a.qseq, a.qcap, pos);
+                            atomicAdd(&ctl->donations, 1ull);
+                            hiv[t] = mid;
+                        }
+                    }
+                    __syncwarp();
+                    break;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace gpm

@@ -378,6 +378,7 @@ gpm_config default_config() {
     c.order = GPM_ORDER_DEGREE_DESC;
     c.max_idle_ms = 120000;
     c.donate = 1;
+    c.donate_after_us = 50;
     return c;
 }
 

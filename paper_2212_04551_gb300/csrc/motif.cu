@@ -1,60 +1,24 @@
-// motif.cu -- induced k-motif counting on the device (Algorithm 4, motif
-// counting; aggregate_pattern of Section 4.3.4).
+// motif.cu -- induced k-motif counting over one graph (Algorithm 4, motif
+// counting; aggregate_pattern of Section 4.3.4).  Hot-path rows A2, A5, A6,
+// A7, A8 and A9; the per-unit walk is in motif_dev.cuh.
 //
-// Hot-path rows A2, A5 (extension step), A6 (pattern aggregation), A7 (per-
-// warp DFS stack in HBM), A8 (work donation) and A9 (counter reduction).
-//
-// The paper extends a traversal from the adjacency of all its vertices
-// (extend(TE, 0, TE.len)), keeps canonical candidates only (filter
-// "canonical", an Arabesque-style test), and at |tr| = k-1 maps every
-// traversal + extension to its pattern through the edge-bitmap dictionary.
-// This kernel reaches the same set of connected induced subgraphs -- each
-// exactly once -- with the exclusive-neighbourhood extension of ESU
-// (Wernicke 2006) instead of re-filtering N(tr) at every level:
-//
-//   * root r = the smallest vertex of the subgraph; ext_1 = {u in N(r): u > r};
-//   * choosing w = ext_l[i] gives ext_{l+1} = ext_l[i+1:] followed by the
-//     exclusive neighbours of w: u in N(w), u > r, u not in the traversal and
-//     not adjacent to any traversal vertex.
-//
-// Per warp, a byte per vertex ("mark", in HBM) records which traversal
-// positions each vertex is adjacent to (bit j <=> adjacent to tr[j]) and
-// whether it is in the traversal (bit 7).  Marks make the exclusivity test
-// and the traversal edge bitmap (the paper's induce step) O(1) per
-// candidate: pushing w marks N(w) once, popping it unmarks N(w).
-//
-// The traversal code is the paper's layout (Section 4.3.4): the v0-v1 edge is
-// implicit, then v_i's edges to v_0..v_{i-1} at bit offset i(i-1)/2 - 1.
-// At |tr| = k-1 -- the last level -- no extension array is built: the k-vertex
-// leaves are (a) the remaining entries of the parent's extension array, whose
-// code bits are read from the marks, and (b) the exclusive neighbours of the
-// newest vertex, whose code is the same for all of them.  Each leaf is looked
-// up in the pattern table and counted in per-block shared counters with one
-// shared atomic per distinct pattern per warp step (__match_any_sync).
+// One persistent launch: each warp takes work units -- a root from a global
+// counter over the root order, or a donated unit from the queue -- and walks
+// it.  Leaves are counted in per-block shared counters and added to the
+// global uint64 counters once per block.  The per-warp marks and extension
+// arrays live in HBM, or in shared memory when the graph is small enough
+// (n bytes of marks plus the arrays per warp).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <string>
 
 #include "common.cuh"
+#include "motif_dev.cuh"
 
 namespace gpm {
 
-constexpr int MT_MAXK = GPM_MOTIF_MAX_K;
-constexpr int MT_LIST = 1024;                  // entries carried by one donated unit
 constexpr unsigned long long MT_QUEUE_CAP = 4096;
-constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns
-
-struct MotifUnit {
-    int32_t root_pos;
-    int32_t depth;              // |tr| of the donated node
-    int32_t len;                // entries in the payload list (its extension array suffix)
-    int32_t child_hi;           // children to expand: list positions [0, child_hi)
-    int32_t sub[MT_MAXK];
-    int32_t list_off;           // >= 0: the list is indices[list_off ..] (a root's own
-                                // extension set); < 0: it is the slot's payload
-};
-static_assert(sizeof(MotifUnit) % 4 == 0, "unit must be word-sized");
 
 struct MotifParams {
     const int32_t* __restrict__ indptr;
@@ -71,61 +35,57 @@ struct MotifParams {
     int32_t* qpayload;          // MT_LIST ints per slot
     unsigned long long qcap;
     unsigned long long* per_root;
-    unsigned char* marks;       // n bytes per warp
-    int32_t* slab;              // slab_ints per warp
+    unsigned char* marks;       // n bytes per warp (HBM variant)
+    int32_t* slab;              // slab_ints per warp (HBM variant)
     long long slab_ints;
     long long lvl_off[MT_MAXK + 1];   // start of ext_l inside a warp's slab
+    int mark_stride;            // shared variant: bytes of marks per warp (16-aligned)
+    int smem_warp_bytes;        // shared variant: marks + slab per warp
     int donate, donate_min;
+    unsigned long long donate_after_ns;
     unsigned long long max_idle_ns;
     unsigned long long* counts; // npat global counters
 };
 
-struct MtWarp {                 // per-warp shared state
-    int sub[MT_MAXK + 1];
-    int code[MT_MAXK + 1];      // traversal code of tr[0..l-1]
-    int cur[MT_MAXK + 1];
-    int hi[MT_MAXK + 1];
-    int len[MT_MAXK + 1];
-    unsigned long long qpos;    // claimed queue position of a donated unit
-    MotifUnit unit;
-};
-
-__device__ __forceinline__ int code_off(int i) { return i * (i - 1) / 2 - 1; }   // bits of v_i, i >= 2
-
-// count one leaf per active lane under pattern pid (warp-aggregated shared atomics)
-__device__ __forceinline__ void count_leaves(unsigned long long* bcnt, bool active, int pid, int* err_flag) {
-    const int key = active ? pid : -1;
-    const unsigned grp = __match_any_sync(GPM_FULL_MASK, key);
-    const int lane = threadIdx.x & 31;
-    if (active && lane == __ffs(grp) - 1) {
-        if (pid == 0xffff) atomicExch(err_flag, DEV_EINVAL);
-        else atomicAdd(&bcnt[pid], (unsigned long long)__popc(grp));
-    }
-}
-
-__device__ __forceinline__ void mark_or(unsigned char* mk, const int32_t* __restrict__ indices, int beg, int end,
-                                        unsigned char bit, int lane) {
-    for (int t = beg + lane; t < end; t += 32) mk[indices[t]] |= bit;
-}
-__device__ __forceinline__ void mark_andnot(unsigned char* mk, const int32_t* __restrict__ indices, int beg,
-                                            int end, unsigned char bit, int lane) {
-    for (int t = beg + lane; t < end; t += 32) mk[indices[t]] &= (unsigned char)~bit;
-}
-
+template <bool SMEM_STATE>
 __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const int nwb = blockDim.x >> 5;
     unsigned long long* bcnt = reinterpret_cast<unsigned long long*>(smem_raw);
     MtWarp* W = reinterpret_cast<MtWarp*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT) + wib;
     for (int j = threadIdx.x; j < p.npat; j += blockDim.x) bcnt[j] = 0ull;
-    __syncthreads();
 
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
-    unsigned char* mk = p.marks + gw * (long long)p.n;
-    int32_t* slab = p.slab + gw * p.slab_ints;
+    const long long gw = (long long)blockIdx.x * nwb + wib;
     Control* ctl = p.ctl;
-    const int k = p.k;
+    MotifWalk a;
+    a.indptr = p.indptr;
+    a.indices = p.indices;
+    a.lut = p.lut;
+    a.k = p.k;
+    a.mbase = 0;
+    a.lvl_off = p.lvl_off;
+    a.ctl = ctl;
+    a.qseq = p.qseq;
+    a.qunits = p.qunits;
+    a.qpayload = p.qpayload;
+    a.qcap = p.qcap;
+    a.donate_min = p.donate_min;
+    a.donate_after_ns = p.donate_after_ns;
+    a.err = &ctl->error;
+    if (SMEM_STATE) {
+        unsigned char* tail = smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb;
+        tail = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tail) + 15) & ~uintptr_t(15));
+        a.mk = tail + (size_t)wib * p.smem_warp_bytes;
+        a.slab = reinterpret_cast<int32_t*>(a.mk + p.mark_stride);
+        for (int v = lane; v < p.mark_stride; v += 32) a.mk[v] = 0;
+    } else {
+        a.mk = p.marks + gw * (long long)p.n;
+        a.slab = p.slab + gw * p.slab_ints;
+    }
+    __syncthreads();
+    BlockSink sink{bcnt};
     const int32_t* __restrict__ indptr = p.indptr;
     const int32_t* __restrict__ indices = p.indices;
 
@@ -199,35 +159,15 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
         if (lane == 0)
             for (int j = 0; j < pdepth; j++) W->sub[j] = W->unit.sub[j];
         __syncwarp();
-        // marks of the prefix: bit j on N(tr[j]), bit 7 on tr itself
-        for (int j = 0; j < pdepth; j++) {
-            const int v = W->sub[j];
-            mark_or(mk, indices, indptr[v], indptr[v + 1], (unsigned char)(1u << j), lane);
-            __syncwarp();
-        }
-        if (lane < pdepth) mk[W->sub[lane]] |= 0x80;
-        __syncwarp();
-        if (lane == 0) {
-            W->code[1] = 0;
-            W->code[2] = 0;
-            for (int i = 2; i < pdepth; i++)
-                W->code[i + 1] = W->code[i] | ((mk[W->sub[i]] & ((1 << i) - 1)) << code_off(i));
-        }
-        // extension array of the unit's node: for a root, the suffix of N(r)
-        // above r (lists are sorted); for a donated unit, its payload list
+        mt_setup_prefix(a, W, pdepth, lane);
         const int32_t* unit_ext;
         if (kind == 1) {
-            const int b = indptr[root], e = indptr[root + 1];
-            int lo = b, hi = e;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (indices[mid] <= root) lo = mid + 1; else hi = mid;
-            }
+            const int lo = mt_root_ext_begin(indptr, indices, root);
             unit_ext = indices + lo;
             if (lane == 0) {
-                W->len[1] = e - lo;
+                W->len[1] = indptr[root + 1] - lo;
                 W->cur[1] = 0;
-                W->hi[1] = e - lo;
+                W->hi[1] = indptr[root + 1] - lo;
             }
         } else if (W->unit.list_off >= 0) {
             // pre-split seed: the list is a suffix of the root's adjacency
@@ -239,7 +179,7 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                 W->hi[pdepth] = W->unit.child_hi;
             }
         } else {
-            int32_t* dst = slab + p.lvl_off[pdepth];
+            int32_t* dst = a.slab + p.lvl_off[pdepth];
             const long long slot = (long long)(W->qpos % p.qcap);
             const int32_t* src = p.qpayload + slot * MT_LIST;
             const int len = W->unit.len;
@@ -256,167 +196,14 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
         }
         __syncwarp();
 
-        // ---------------------------------------------------------- DFS
         unsigned long long unit_leaves = 0;   // lane-private
-        int l = pdepth;
-        int iter = 0;
-        for (;;) {
-            const int c = W->cur[l];
-            if (c >= W->hi[l]) {
-                if (l == pdepth) break;
-                // pop tr[l-1] (pushed at depth l-1)
-                const int w = W->sub[l - 1];
-                mark_andnot(mk, indices, indptr[w], indptr[w + 1], (unsigned char)(1u << (l - 1)), lane);
-                __syncwarp();
-                if (lane == 0) mk[w] &= 0x7f;
-                __syncwarp();
-                l--;
-                continue;
-            }
-            const int32_t* ext = l == pdepth ? unit_ext : slab + p.lvl_off[l];
-            const int w = ext[c];
-            if (lane == 0) W->cur[l] = c + 1;
-            const int sigw = mk[w] & ((1 << l) - 1);
-            const int codew = l >= 2 ? (W->code[l] | (sigw << code_off(l))) : 0;
-            const int wb = indptr[w], we = indptr[w + 1];
-            const unsigned char low = (unsigned char)(0x80 | ((1u << l) - 1));
-            if (l + 1 == k - 1) {
-                // ---- last level: leaves of the (k-1)-set tr + w
-                const int offk = code_off(l + 1);
-                int excl = 0;
-                for (int t = wb + lane; t < we; t += 32) {
-                    const int x = indices[t];
-                    const unsigned char m = mk[x];
-                    excl += (x > root && (m & low) == 0) ? 1 : 0;
-                    mk[x] = m | (unsigned char)(1u << l);
-                }
-                excl = __reduce_add_sync(GPM_FULL_MASK, (unsigned)excl);
-                __syncwarp();
-                if (excl) {
-                    const int pid = p.lut[codew | ((1 << l) << offk)];
-                    if (lane == 0) {
-                        if (pid == 0xffff) atomicExch(&ctl->error, DEV_EINVAL);
-                        else atomicAdd(&bcnt[pid], (unsigned long long)excl);
-                    }
-                    if (lane == 0) unit_leaves += (unsigned)excl;
-                }
-                const int len = W->len[l];
-                const unsigned lowk = (1u << (l + 1)) - 1u;
-                for (int j0 = c + 1; j0 < len; j0 += 32) {
-                    const int j = j0 + lane;
-                    const bool act = j < len;
-                    int pid = 0;
-                    if (act) {
-                        const int x = ext[j];
-                        const int sig = mk[x] & lowk;
-                        pid = p.lut[codew | (sig << offk)];
-                        unit_leaves++;
-                    }
-                    count_leaves(bcnt, act, pid, &ctl->error);
-                }
-                __syncwarp();
-                mark_andnot(mk, indices, wb, we, (unsigned char)(1u << l), lane);
-                __syncwarp();
-            } else {
-                // ---- push w: ext_{l+1} = ext_l[c+1:] ++ exclusive neighbours of w
-                int32_t* nxt = slab + p.lvl_off[l + 1];
-                const int len = W->len[l];
-                const int inh = len - (c + 1);
-                for (int t = lane; t < inh; t += 32) nxt[t] = ext[c + 1 + t];
-                int n_new = inh;
-                for (int t0 = wb; t0 < we; t0 += 32) {
-                    const int t = t0 + lane;
-                    bool ex = false;
-                    int x = 0;
-                    if (t < we) {
-                        x = indices[t];
-                        const unsigned char m = mk[x];
-                        ex = x > root && (m & low) == 0;
-                        mk[x] = m | (unsigned char)(1u << l);
-                    }
-                    const unsigned bal = __ballot_sync(GPM_FULL_MASK, ex);
-                    if (ex) nxt[n_new + __popc(bal & gpm_lanemask_lt())] = x;
-                    n_new += __popc(bal);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    mk[w] |= 0x80;
-                    W->sub[l] = w;
-                    W->code[l + 1] = codew;
-                    W->len[l + 1] = n_new;
-                    W->cur[l + 1] = 0;
-                    W->hi[l + 1] = n_new;
-                }
-                __syncwarp();
-                l++;
-            }
-
-            if ((++iter & 7) == 0) {
-                int err = 0, want = 0;
-                if (lane == 0) {
-                    err = *(volatile int*)&ctl->error;
-                    if (p.donate) {
-                        const int idl = *(volatile int*)&ctl->idle;
-                        const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
-                        const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
-                        want = idl > 0 && (long long)(qt - qh) < (long long)idl;
-                    }
-                }
-                err = __shfl_sync(GPM_FULL_MASK, err, 0);
-                if (err) { aborted = true; break; }
-                want = __shfl_sync(GPM_FULL_MASK, want, 0);
-                if (want) {
-                    for (int t = pdepth; t <= l; t++) {
-                        const int from = W->cur[t], to = W->hi[t], len = W->len[t];
-                        const int rem = to - from;
-                        if (rem < max(p.donate_min, 2)) continue;
-                        int start = from + (rem - rem / 2);
-                        start = max(start, len - MT_LIST);
-                        if (start >= to) continue;
-                        unsigned long long pos = 0;
-                        int ok = 0;
-                        if (lane == 0) ok = gpm_q_reserve(p.qseq, p.qcap, &ctl->q_tail, &pos) ? 1 : 0;
-                        ok = __shfl_sync(GPM_FULL_MASK, ok, 0);
-                        if (!ok) break;
-                        pos = __shfl_sync(GPM_FULL_MASK, pos, 0);
-                        const long long slot = (long long)(pos % p.qcap);
-                        int32_t* dst = p.qpayload + slot * MT_LIST;
-                        const int32_t* src = t == pdepth ? unit_ext : slab + p.lvl_off[t];
-                        for (int z = start + lane; z < len; z += 32) dst[z - start] = src[z];
-                        if (lane == 0) {
-                            MotifUnit u;
-                            u.root_pos = root_pos;
-                            u.depth = t;
-                            u.len = len - start;
-                            u.child_hi = to - start;
-                            for (int z = 0; z < MT_MAXK; z++) u.sub[z] = z < t ? W->sub[z] : -1;
-                            u.list_off = -1;
-                            p.qunits[slot] = u;
-                            W->hi[t] = start;
-                            atomicAdd((unsigned long long*)&ctl->pending, 1ull);
-                        }
-                        __threadfence();
-                        __syncwarp();
-                        if (lane == 0) {
-                            gpm_q_publish(p.qseq, p.qcap, pos);
-                            atomicAdd(&ctl->donations, 1ull);
-                        }
-                        __syncwarp();
-                        break;
-                    }
-                }
-            }
+        const bool ok = p.donate ? mt_walk<true>(a, W, pdepth, root, root_pos, unit_ext, sink, unit_leaves, lane)
+                                 : mt_walk<false>(a, W, pdepth, root, root_pos, unit_ext, sink, unit_leaves, lane);
+        if (!ok) {
+            aborted = true;   // HBM marks are left dirty: the host re-clears them after an error
+            break;
         }
-        if (aborted) break;   // marks are left dirty: the host re-clears them after an error
-
-        // clear the prefix marks (deeper marks were undone by the pops)
-        for (int j = 0; j < pdepth; j++) {
-            const int v = W->sub[j];
-            for (int t = indptr[v] + lane; t < indptr[v + 1]; t += 32) mk[indices[t]] = 0;
-            __syncwarp();
-        }
-        if (lane < pdepth) mk[W->sub[lane]] = 0;
-        __syncwarp();
+        mt_clear_prefix(a, W, pdepth, lane);
 
         if (p.per_root) {
             const unsigned long long tot = gpm_warp_sum(unit_leaves);
@@ -526,10 +313,6 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
 
     const uint16_t* lut = device_lut(k);
     const int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block : 8;
-    const size_t smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb;
-    GPM_CUDA(cudaFuncSetAttribute(k_motif, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    Grid gr = plan_grid(g, (const void*)k_motif, wpb, smem);
-    const long long nw = gr.total_warps();
 
     MotifParams p{};
     p.indptr = g->indptr.as<int32_t>();
@@ -549,18 +332,32 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
         off = (off + 3) & ~3ll;
     }
     p.slab_ints = std::max(off, 4ll);
-    g->scratch_slab.ensure(sizeof(int32_t) * p.slab_ints * nw);
-    const size_t mark_bytes = (size_t)g->n * nw;
-    if (g->scratch_mark.bytes < mark_bytes || !g->scratch_mark.ptr) {
-        g->scratch_mark.ensure(mark_bytes);
-        g->mark_bytes_cleared = 0;
+
+    // per-warp state in shared memory when it is small (marks + arrays)
+    const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
+    p.mark_stride = (int)((g->n + 15) & ~15);
+    const long long warp_state = (long long)p.mark_stride + 4 * p.slab_ints;
+    const bool smem_state = warp_state <= 12 * 1024 && base_smem + (size_t)wpb * warp_state <= 200 * 1024;
+    p.smem_warp_bytes = (int)((warp_state + 15) & ~15ll);
+    const size_t smem = base_smem + (smem_state ? (size_t)wpb * p.smem_warp_bytes : 0);
+    const void* kfun = smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>;
+    GPM_CUDA(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    Grid gr = plan_grid(g, kfun, wpb, smem);
+    const long long nw = gr.total_warps();
+    if (!smem_state) {
+        g->scratch_slab.ensure(sizeof(int32_t) * p.slab_ints * nw);
+        const size_t mark_bytes = (size_t)g->n * nw;
+        if (g->scratch_mark.bytes < mark_bytes || !g->scratch_mark.ptr) {
+            g->scratch_mark.ensure(mark_bytes);
+            g->mark_bytes_cleared = 0;
+        }
+        if (g->mark_bytes_cleared < mark_bytes) {
+            GPM_CUDA(cudaMemsetAsync(g->scratch_mark.ptr, 0, g->scratch_mark.bytes, s));
+            g->mark_bytes_cleared = g->scratch_mark.bytes;
+        }
+        p.marks = g->scratch_mark.as<unsigned char>();
+        p.slab = g->scratch_slab.as<int32_t>();
     }
-    if (g->mark_bytes_cleared < mark_bytes) {
-        GPM_CUDA(cudaMemsetAsync(g->scratch_mark.ptr, 0, g->scratch_mark.bytes, s));
-        g->mark_bytes_cleared = g->scratch_mark.bytes;
-    }
-    p.marks = g->scratch_mark.as<unsigned char>();
-    p.slab = g->scratch_slab.as<int32_t>();
 
     g->scratch_small.ensure(sizeof(Control) + sizeof(unsigned long long) * MT_MAXPAT);
     Control* ctl = g->scratch_small.as<Control>();
@@ -587,11 +384,13 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.per_root = d_per_root;
     p.donate = g->cfg.donate;
     p.donate_min = std::max(2, g->cfg.donate_min);
+    p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
     p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
 
     if (n_roots > 0) {
         GPM_CUDA(cudaEventRecord(g->ev0, s));
-        k_motif<<<gr.blocks, wpb * 32, smem, s>>>(p);
+        if (smem_state) k_motif<true><<<gr.blocks, wpb * 32, smem, s>>>(p);
+        else k_motif<false><<<gr.blocks, wpb * 32, smem, s>>>(p);
         GPM_CUDA(cudaGetLastError());
         GPM_CUDA(cudaEventRecord(g->ev1, s));
         st.grid_blocks = gr.blocks;

@@ -43,7 +43,8 @@ class GpmError(RuntimeError):
 class gpm_config(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("donate_min", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32)]
+                ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
+                ("donate_after_us", ctypes.c_int32)]
 
 
 class gpm_stats(ctypes.Structure):
@@ -82,6 +83,13 @@ SIGNATURES = {
     "gpm_sched_from_scores": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i32p, ctypes.c_int64, ctypes.c_int32,
                                              ctypes.c_int32]),
     "gpm_count_scheduled": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int64, _u64p]),
+    "gpm_batch_create": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]),
+    "gpm_batch_destroy": (None, [_vp]),
+    "gpm_batch_count": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, _u64p]),
+    "gpm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(gpm_config), ctypes.POINTER(ctypes.c_double)]),
+    "gpm_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
+    "gpm_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
 }
 GPM_MLP_PARAMS = 4801
 
@@ -332,3 +340,101 @@ def gpm_count_scheduled(g: Graph, app: int, k: int, n_roots: int | None = None, 
                                       pr.ctypes.data_as(_u64p) if pr is not None else None),
            "gpm_count_scheduled")
     return counts, (pr[:n_roots] if pr is not None else None)
+
+
+# ------------------------------------------------------- batched launch
+
+class Batch:
+    """Owning handle of a gpm_batch."""
+
+    def __init__(self, handle: int, n_graphs: int, keep=()):
+        self.handle = handle
+        self.n_graphs = n_graphs
+        self._keep = keep
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gpm_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+
+def gpm_batch_create(graph_off, indptr, indices, flags: int = 0, stream=None) -> Batch:
+    lib = load()
+    pg, kg, dg_ = _array_ptr(graph_off, np.int32)
+    pi, ki, di = _array_ptr(indptr, np.int32)
+    px, kx, dx = _array_ptr(indices, np.int32)
+    if not (dg_ == di == dx):
+        raise ValueError("all arrays must be host or all device")
+    if di:
+        flags |= GPM_DEVICE_PTRS
+    n_graphs = int(graph_off.shape[0]) - 1
+    out = ctypes.c_void_p()
+    _check(lib.gpm_batch_create(pg, pi, px, n_graphs, int(flags), _stream_handle(stream), ctypes.byref(out)),
+           "gpm_batch_create")
+    return Batch(out.value, n_graphs, keep=(kg, ki, kx))
+
+
+def gpm_batch_destroy(b: Batch) -> None:
+    b.close()
+
+
+def gpm_batch_count(b: Batch, clique_k: int, motif_k: int):
+    """(clique counts [G] or None, motif counts [G, P] or None)."""
+    G = b.n_graphs
+    cc = np.zeros(max(G, 1), dtype=np.uint64) if clique_k else None
+    npat = gpm_motif_num_patterns(motif_k) if motif_k else 0
+    mc = np.zeros((max(G, 1), max(npat, 1)), dtype=np.uint64) if motif_k else None
+    _check(load().gpm_batch_count(b, int(clique_k), int(motif_k),
+                                  cc.ctypes.data_as(_u64p) if cc is not None else None,
+                                  mc.ctypes.data_as(_u64p) if mc is not None else None), "gpm_batch_count")
+    return (cc[:G] if cc is not None else None), (mc[:G, :npat] if mc is not None else None)
+
+
+def gpm_batch_autotune(b: Batch, clique_k: int, motif_k: int, reps: int = 3):
+    c = gpm_config()
+    ms = ctypes.c_double()
+    _check(load().gpm_batch_autotune(b, int(clique_k), int(motif_k), int(reps), ctypes.byref(c), ctypes.byref(ms)),
+           "gpm_batch_autotune")
+    return {f: getattr(c, f) for f, _ in gpm_config._fields_}, ms.value
+
+
+def gpm_batch_set_config(b: Batch, **kw) -> None:
+    c = gpm_config()
+    c.warps_per_block = 8
+    c.donate_min = 4
+    c.order = GPM_ORDER_DEGREE_DESC
+    c.max_idle_ms = 120000
+    c.donate = 1
+    c.donate_after_us = 50
+    for key, val in kw.items():
+        setattr(c, key, int(val))
+    _check(load().gpm_batch_set_config(b, ctypes.byref(c)), "gpm_batch_set_config")
+
+
+def gpm_batch_get_stats(b: Batch) -> dict:
+    s = gpm_stats()
+    _check(load().gpm_batch_get_stats(b, ctypes.byref(s)), "gpm_batch_get_stats")
+    return {f: getattr(s, f) for f, _ in gpm_stats._fields_}
+
+
+def batch_from_graphs(graph_list, stream=None) -> Batch:
+    """Pack a list of ``graphs.CSR`` (local ids) into one batch (global ids)."""
+    goff = np.zeros(len(graph_list) + 1, dtype=np.int64)
+    goff[1:] = np.cumsum([g.n for g in graph_list])
+    ip_parts = [np.zeros(1, dtype=np.int64)]
+    ix_parts = []
+    eoff = 0
+    for g, base in zip(graph_list, goff[:-1]):
+        ip_parts.append(g.indptr[1:].astype(np.int64) + eoff)
+        ix_parts.append(g.indices.astype(np.int64) + base)
+        eoff += g.indices.shape[0]
+    indptr = np.concatenate(ip_parts).astype(np.int32)
+    indices = (np.concatenate(ix_parts) if ix_parts else np.zeros(0, dtype=np.int64)).astype(np.int32)
+    return gpm_batch_create(goff.astype(np.int32), indptr, indices, stream=stream)
