@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--k-hi", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the learned and batched comparisons")
     return ap.parse_args()
 
 
@@ -61,6 +62,44 @@ def peaks():
             p = json.load(f)
         return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
     return 6800.0, 2070.0, "fallback"
+
+
+# The clique kernel's unit of work is one 32-bit candidate-word operation:
+# AND of a candidate word with an adjacency-row word, POPC, accumulate.  Its
+# peak is set by the population-count rate: 16 results per clock per SM
+# (the integer-intrinsic throughput of the CUDA arithmetic-instruction table)
+# x 152 SMs x the maximum SM clock.
+POPC_PER_CLK_PER_SM = 16
+
+
+def kernel_source_hash(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2212_04551_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary: str, src_hash: str, units_now: float):
+    """DRAM bytes per launch from a committed ncu summary, scaled to this
+    launch's units, or None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != src_hash:
+        return None
+    try:
+        t = float(kv["dram_bytes_per_launch"])
+        u = float(kv["units_per_launch"])
+    except (KeyError, ValueError):
+        return None
+    return t * (units_now / u) if u > 0 else None
 
 
 class ClockSampler:
@@ -153,6 +192,115 @@ def cpu_baseline(g, k_lo, k_hi, budget_s):
     return found / el, desc, done
 
 
+def timed(fn, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def learned_vs_plain(stream, k: int = 5, n_roots: int = 1024, epochs: int = 60, reps: int = 3) -> dict:
+    """Learned scheduling (the MLP trained on R-MAT scale-12 graphs, seeds
+    100-131, with per-root sizes measured by the plain enumerator) against the
+    plain heaviest-degree-first donation scheduler, on the R-MAT scale-16 graph
+    restricted to a seeded sample of roots (ids >= 1024, degree <= 32);
+    counts must agree exactly."""
+    import torch
+
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    from paper_2212_04551_gb300 import learned as L
+    t0 = time.perf_counter()
+    X, T = L.training_set(gpm.GPM_APP_MOTIF, k, seeds=range(100, 132), scale=12, stream=stream)
+    t_labels = time.perf_counter() - t0
+    model = L.new_model(0, stream)
+    untrained = L.new_model(0, stream)
+    t0 = time.perf_counter()
+    L.train(model, X, T, epochs=epochs, batch=4096, lr=3e-3, stream=stream)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    g = G.workload("rmat16")
+    d = g.degrees()
+    ok = (np.arange(g.n) >= 1024) & (d <= 32)
+    roots = G.sample_roots(g.n, n_roots, seed=25, exclude=~ok)
+    dg = gpm.graph_from_csr(g, stream=stream)
+    feats = L.features(dg, g.n)
+    warps = None
+    res = {}
+    ref = None
+    sizes = None
+    for name, scorer in (("plain", None), ("learned", model), ("untrained", untrained)):
+        if scorer is None:
+            gpm.gpm_sched_from_scores(dg, gpm.GPM_APP_MOTIF, None, roots, 0, 0)
+            plan = {"split_roots": 0, "chunks": 0}
+        else:
+            pred = L.predict(scorer, feats, stream)
+            if warps is None:
+                warps = gpm.gpm_get_stats(dg)["grid_blocks"] * gpm.gpm_get_stats(dg)["warps_per_block"] or 4864
+            plan = L.schedule(dg, gpm.GPM_APP_MOTIF, pred, roots, warps=warps, chunks=8)
+        times = []
+        for _ in range(reps):
+            (c, pr), ms = timed(lambda: gpm.gpm_count_scheduled(dg, gpm.GPM_APP_MOTIF, k, n_roots=len(roots),
+                                                                per_root=True), stream)
+            times.append(ms)
+        st = gpm.gpm_get_stats(dg)
+        if ref is None:
+            ref, sizes = c, pr
+        assert np.array_equal(c, ref), f"{name} schedule changed the counts"
+        total = int(c.sum())
+        ms = statistics.median(times)
+        res[name] = {"ms": ms, "subgraphs_per_s": total / (ms / 1000.0), "donations": int(st["donations"]),
+                     "units": int(st["units_done"]), **plan}
+        if scorer is not None:
+            p = L.predict(scorer, feats, stream).cpu().numpy()[roots]
+            from scipy.stats import spearmanr
+            res[name]["spearman_vs_measured"] = float(spearmanr(p, np.log1p(sizes.astype(np.float64))).statistic)
+    res["k"] = k
+    res["roots"] = f"{len(roots)} seeded roots of rmat16 (id >= 1024, degree <= 32)"
+    res["subgraphs"] = int(ref.sum())
+    res["train"] = {"samples": int(X.shape[0]), "epochs": epochs, "label_s": round(t_labels, 2),
+                    "train_s": round(t_train, 2), "final_mse": model.history[-1], "first_mse": model.history[0]}
+    res["speedup_learned_vs_plain"] = res["plain"]["ms"] / res["learned"]["ms"]
+    dg.close()
+    return res
+
+
+def batched_vs_plain(stream, reps: int = 5) -> dict:
+    """4,096 Barabasi-Albert graphs, per-graph 4-clique and 5-motif counts:
+    one autotuned, CUDA-graph-captured persistent launch against the plain
+    form (one gpm_clique_count + one gpm_motif_count per graph)."""
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    gs = G.workload("ba4096")
+    b = gpm.batch_from_graphs(gs, stream=stream)
+    best, _ = gpm.gpm_batch_autotune(b, 4, 5, reps=3)
+    cc, mc = gpm.gpm_batch_count(b, 4, 5)
+    times = []
+    for _ in range(reps):
+        _, ms = timed(lambda: gpm.gpm_batch_count(b, 4, 5), stream)
+        times.append(ms)
+    total = int(cc.sum()) + int(mc.sum())
+    t_b = statistics.median(times)
+    # plain: every graph on its own, graphs resident on the device
+    dgs = [gpm.graph_from_csr(g, stream=stream) for g in gs]
+    def plain():
+        c = np.array([gpm.gpm_clique_count(d, 4) for d in dgs], dtype=np.uint64)
+        m = np.stack([gpm.gpm_motif_count(d, 5) for d in dgs])
+        return c, m
+    (pc, pm), t_p = timed(plain, stream)
+    assert np.array_equal(pc, cc) and np.array_equal(pm, mc), "batched counts differ from per-graph counts"
+    for d in dgs:
+        d.close()
+    b.close()
+    return {"graphs": len(gs), "subgraphs": total, "batched_ms": t_b, "plain_ms": t_p,
+            "batched_subgraphs_per_s": total / (t_b / 1000.0), "plain_subgraphs_per_s": total / (t_p / 1000.0),
+            "speedup": t_p / t_b, "autotuned": best}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -219,7 +367,7 @@ def main():
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    step_ms, kern_ms = [], []
+    step_ms, kern_ms, word_ops = [], [], []
     launches = 0
     t_wall = time.perf_counter()
     for _ in range(args.steps):
@@ -233,7 +381,8 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         st = gpm.gpm_get_stats(dg)
         kern_ms.append(st["kernel_ms"])
-        launches += int(st.get("kernel_launches", 2))
+        word_ops.append(float(st["word_ops"]))
+        launches += int(st["kernel_launches"])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -267,13 +416,22 @@ def main():
         assert [int(x) for x in c2] == [int(x) for x in counts], "end-to-end counts differ"
     e2e_value = total / (statistics.mean(e2e_ms) / 1000.0)
 
-    # roofline of the dominant kernel (k_clique): algorithmic bytes per
-    # launch = the sorted-list bytes a merge-based enumerator must read for
-    # the same search (4 B x (|C| + d+) per extension), counted once by the
-    # instrumented oracle formula on the whole graph is too slow, so the
-    # kernel reports its own count of candidate-set words instead -- see the
-    # design notes; here the bound is the ALU/shared-memory roofline.
+    # roofline of the dominant kernel (k_clique): ALU-bound on population
+    # counts of candidate words; achieved = word operations per launch (the
+    # kernel counts them exactly) / the launch's CUDA-event time
     hbm, sm_max, peak_kind = peaks()
+    import torch as _t
+    sms = _t.cuda.get_device_properties(local_rank).multi_processor_count
+    peak_ops = sms * POPC_PER_CLK_PER_SM * sm_max * 1e6
+    wops = statistics.mean(word_ops)
+    achieved = wops / (statistics.mean(kern_ms) / 1000.0)
+    src_hash = kernel_source_hash(["clique.cu", "clique_dev.cuh", "common.cuh"])
+    roofline = {"bound": "alu", "kernel": "k_clique", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+                "unit": "Gop/s (32-bit candidate-word AND+POPC)", "frac": achieved / peak_ops,
+                "peak_kind": f"derived: {sms} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz ({peak_kind} clock)",
+                "units_per_launch": wops,
+                "traffic": profiled_traffic("k_clique_chunglu1m.txt", src_hash, wops),
+                "kernel_source_sha": src_hash}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -284,8 +442,11 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_ip.nbytes + h_ix.nbytes),
                 "d2h_bytes_per_step": 8 * len(kk), "ms_per_step": statistics.mean(e2e_ms)},
         "clocks": clocks, "gpu_launches": launches,
-        "roofline": None,
+        "roofline": roofline,
     }
+    if rank == 0 and world == 1 and not args.no_variants:
+        line["batched_vs_plain"] = batched_vs_plain(stream)
+        line["learned_vs_plain"] = learned_vs_plain(stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}

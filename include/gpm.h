@@ -153,7 +153,7 @@ gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, i
  * work is split and ordered (Section 4.3.5 replaced by in-kernel donation).
  */
 typedef struct {
-    int32_t warps_per_block;   /* 4, 8, 16 or 32 (0 = default 8)                       */
+    int32_t warps_per_block;   /* 1, 2, 4, 8 or 16 (0 = default 8)                     */
     int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum)       */
     int32_t donate_min;        /* split a level only if >= this many siblings remain  */
     int32_t order;             /* GPM_ORDER_* root order of the plain scheduler         */
@@ -178,6 +178,8 @@ typedef struct {
     uint64_t idle_polls;       /* times an idle warp polled the queue             */
     int32_t  grid_blocks;      /* persistent grid size                            */
     int32_t  warps_per_block;
+    uint64_t word_ops;         /* clique: 32-bit candidate-word AND+POPC operations */
+    int32_t  kernel_launches;  /* kernels the call launched (enumeration path)    */
 } gpm_stats;
 
 gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
@@ -282,7 +284,7 @@ gpm_status gpm_batch_count(gpm_batch* b, int clique_k, int motif_k, uint64_t* cl
 
 /*
  * Autotune the launch shape for (clique_k, motif_k): warps per block {2, 4,
- * 8, 16, 32} x resident blocks per SM {max, 1, 2} x unit order {tasks
+ * 8, 16} x resident blocks per SM {max, 1, 2} x unit order {tasks
  * grouped, merged}, each timed as the median of `reps` replays; the fastest
  * is kept for this batch (and cached in-process for batches of the same
  * shape).  best (nullable) receives it; best_ms (nullable) its median time,

@@ -46,15 +46,13 @@ struct gpm_batch {
     gpm_stats stats{};
     struct Captured {
         cudaGraphExec_t exec = nullptr;
+        gpm::DevBuf units;           // this launch's unit list (baked into the graph)
         gpm::DevBuf dev_out;         // [G] clique + [G*npat] motif + Control
         unsigned long long* host_out = nullptr;   // pinned
         size_t words = 0;
         int blocks = 0, wpb = 0;
     };
     std::map<std::tuple<int, int, int, int, int>, Captured> graphs;   // (kc, km, wpb, bps, order)
-    gpm::DevBuf units;               // unit list per order mode
-    int units_mode = -1, units_kc = -1, units_km = -1;
-    long long n_units = 0;
 };
 
 namespace gpm {
@@ -164,8 +162,8 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
                 unit->hi = -1;
             }
             __syncwarp();
-            unsigned long long km1 = 0;
-            cq_walk<false>(cw, unit, 0, r, d, cached_root, sum, km1, lane);
+            unsigned long long km1 = 0, wops = 0;
+            cq_walk<false>(cw, unit, 0, r, d, cached_root, sum, km1, wops, lane);
             sum = gpm_warp_sum(sum);
             if (lane == 0 && sum) {
                 const unsigned long long old = atomicAdd(&p.clique_out[gidx], sum);
@@ -206,7 +204,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
 // first), then every clique root (heaviest out-degree first).  Mode 1: both
 // tasks merged into one heaviest-first list (weights: degree for motif units,
 // out-degree for clique units, scaled to a common range).
-static void build_units(gpm_batch* b, int kc, int km, int mode) {
+static long long build_units(gpm_batch* b, int kc, int km, int mode, gpm::DevBuf& out) {
     gpm_graph* g = b->g;
     const int n = g->n;
     std::vector<int32_t> deg(n), od(n);
@@ -231,15 +229,12 @@ static void build_units(gpm_batch* b, int kc, int km, int mode) {
     }
     std::vector<int32_t> codes(items.size());
     for (size_t i = 0; i < items.size(); i++) codes[i] = items[i].second;
-    b->units.ensure(sizeof(int32_t) * std::max<size_t>(codes.size(), 1));
+    out.ensure(sizeof(int32_t) * std::max<size_t>(codes.size(), 1));
     if (!codes.empty())
-        GPM_CUDA(cudaMemcpyAsync(b->units.ptr, codes.data(), sizeof(int32_t) * codes.size(), cudaMemcpyHostToDevice,
+        GPM_CUDA(cudaMemcpyAsync(out.ptr, codes.data(), sizeof(int32_t) * codes.size(), cudaMemcpyHostToDevice,
                                  b->stream));
     GPM_CUDA(cudaStreamSynchronize(b->stream));
-    b->n_units = (long long)codes.size();
-    b->units_mode = mode;
-    b->units_kc = kc;
-    b->units_km = km;
+    return (long long)codes.size();
 }
 
 static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
@@ -251,7 +246,8 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     if (it != b->graphs.end()) return it->second;
 
     if (kc > 0) ensure_dag(g);
-    if (b->units_mode != b->order_mode || b->units_kc != kc || b->units_km != km) build_units(b, kc, km, b->order_mode);
+    DevBuf units;
+    const long long n_units = build_units(b, kc, km, b->order_mode, units);
     const int npat = km > 0 ? (int)pattern_table(km).num_patterns : 0;
 
     BatchParams p{};
@@ -262,8 +258,8 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     p.outdeg = kc > 0 ? g->dag_outdeg.as<int32_t>() : nullptr;
     p.goff = b->goff.as<int32_t>();
     p.vgraph = b->vgraph.as<int32_t>();
-    p.units = b->units.as<int32_t>();
-    p.n_units = b->n_units;
+    p.units = units.as<int32_t>();
+    p.n_units = n_units;
     p.kc = kc;
     p.km = km;
     p.npat = npat;
@@ -294,6 +290,7 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     const int blocks = per_sm * g->num_sms;
 
     gpm_batch::Captured& c = b->graphs[key];
+    c.units = std::move(units);
     const size_t G = (size_t)b->n_graphs;
     const size_t ctl_words = (sizeof(Control) + 7) / 8;
     c.words = G + G * npat + ctl_words;
@@ -457,6 +454,7 @@ void batch_count(gpm_batch* b, int kc, int km, uint64_t* clique_counts, uint64_t
     gpm_stats st{};
     st.kernel_ms = ms;
     st.units_done = h->units_done;
+    st.kernel_launches = 1;
     st.grid_blocks = cap.blocks;
     st.warps_per_block = cap.wpb;
     b->stats = st;
@@ -485,7 +483,7 @@ gpm_config batch_autotune(gpm_batch* b, int kc, int km, int reps, double* best_m
     double best_t = 1e300;
     const gpm_config saved = b->cfg;
     for (int mode = 0; mode < 2; mode++)
-        for (int wpb : {2, 4, 8, 16, 32})
+        for (int wpb : {2, 4, 8, 16})
             for (int bps : {0, 1, 2}) {
                 gpm_config c = saved;
                 c.warps_per_block = wpb;
@@ -516,8 +514,8 @@ gpm_config batch_autotune(gpm_batch* b, int kc, int km, int reps, double* best_m
 }
 
 void batch_set_config(gpm_batch* b, const gpm_config& c) {
-    if (c.warps_per_block < 0 || c.warps_per_block > 32 || (c.warps_per_block & (c.warps_per_block - 1)))
-        fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 32]");
+    if (c.warps_per_block < 0 || c.warps_per_block > 16 || (c.warps_per_block & (c.warps_per_block - 1)))
+        fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 16]");
     if (c.blocks_per_sm < 0) fail(GPM_EINVAL, "blocks_per_sm < 0");
     b->cfg = c;
 }

@@ -217,8 +217,8 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         gpm_config c = *cfg;
         if (c.warps_per_block == 0) c.warps_per_block = 8;
         if (c.warps_per_block != 1 && c.warps_per_block != 2 && c.warps_per_block != 4 &&
-            c.warps_per_block != 8 && c.warps_per_block != 16 && c.warps_per_block != 32)
-            fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 32]");
+            c.warps_per_block != 8 && c.warps_per_block != 16)
+            fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 16]");
         if (c.blocks_per_sm < 0) fail(GPM_EINVAL, "blocks_per_sm < 0");
         if (c.donate_min < 0) fail(GPM_EINVAL, "donate_min < 0");
         if (c.order < GPM_ORDER_ID || c.order > GPM_ORDER_CUSTOM) fail(GPM_EINVAL, "unknown order");

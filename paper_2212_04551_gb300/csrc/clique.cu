@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
 
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
     unsigned long long top_km1 = 0;   // lane-private (k_hi-1)-clique count
+    unsigned long long wops = 0;      // lane-private candidate-word operations
     int cached_root = -1;
     bool idle = false;
     unsigned long long polls = 0;
@@ -173,8 +174,8 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
         const int r = p.roots[root_pos];
         const int d = p.outdeg[r];
         unsigned long long unit_sum = 0;   // lane-private k_hi-cliques of this unit
-        const bool ok = p.donate ? cq_walk<true>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, lane)
-                                 : cq_walk<false>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, lane);
+        const bool ok = p.donate ? cq_walk<true>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane)
+                                 : cq_walk<false>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane);
         if (!ok) aborted = true;
         top_sum += unit_sum;
         if (p.per_root) {
@@ -190,8 +191,10 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
 
     const unsigned long long tot = gpm_warp_sum(top_sum);
     const unsigned long long km1 = gpm_warp_sum(top_km1);
+    const unsigned long long wsum = gpm_warp_sum(wops);
     __syncwarp();
     if (lane == 0) {
+        atomicAdd(&ctl->word_ops, wsum);
         if (polls) atomicAdd(&ctl->idle_polls, polls);
         add_count(ctl, p.k_hi, tot);
         if (p.k_hi >= 4 && p.k_hi - 1 >= p.k_lo) add_count(ctl, p.k_hi - 1, km1);
@@ -326,6 +329,8 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
     st.units_done = h.units_done;
     st.donations = h.donations;
     st.idle_polls = h.idle_polls;
+    st.word_ops = h.word_ops;
+    st.kernel_launches = st.grid_blocks ? (n_split > 0 ? 3 : 2) : (k_hi <= 2 && n_roots > 0 ? 1 : 0);
     g->stats = st;
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));

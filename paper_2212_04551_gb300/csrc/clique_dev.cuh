@@ -164,7 +164,8 @@ __device__ __forceinline__ int cq_compact(const uint32_t* C, int w, int from, in
 // through (i, j), aggregate_counter on each (k-1)-clique.  W >= w words.
 template <int W>
 __device__ __forceinline__ void cq_tail2(const uint32_t* C, const uint32_t* rows, int w, int ws, const int* list,
-                                         int nchild, unsigned long long& km1, unsigned long long& kk, int lane) {
+                                         int nchild, unsigned long long& km1, unsigned long long& kk,
+                                         unsigned long long& wops, int lane) {
     uint32_t c[W];
 #pragma unroll
     for (int q = 0; q < W; q++) c[q] = q < w ? C[q] : 0u;
@@ -178,6 +179,7 @@ __device__ __forceinline__ void cq_tail2(const uint32_t* C, const uint32_t* rows
             g += __popc(ci[q]);
         }
         km1 += (unsigned)g;
+        wops += (unsigned long long)(g + 1) * (unsigned)w;
         unsigned acc = 0;
         for (int q = 0; q < w; q++) {
             // word q of C_i without dynamic register indexing
@@ -200,14 +202,14 @@ __device__ __forceinline__ void cq_tail2(const uint32_t* C, const uint32_t* rows
 
 __device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint32_t* rows, int w, int ws,
                                                   const int* list, int nchild, unsigned long long& km1,
-                                                  unsigned long long& kk, int lane) {
-    if (w <= 1) cq_tail2<1>(C, rows, w, ws, list, nchild, km1, kk, lane);
-    else if (w <= 2) cq_tail2<2>(C, rows, w, ws, list, nchild, km1, kk, lane);
-    else if (w <= 4) cq_tail2<4>(C, rows, w, ws, list, nchild, km1, kk, lane);
-    else if (w <= 6) cq_tail2<6>(C, rows, w, ws, list, nchild, km1, kk, lane);
-    else if (w <= 8) cq_tail2<8>(C, rows, w, ws, list, nchild, km1, kk, lane);
-    else if (w <= 10) cq_tail2<10>(C, rows, w, ws, list, nchild, km1, kk, lane);
-    else if (w <= 16) cq_tail2<16>(C, rows, w, ws, list, nchild, km1, kk, lane);
+                                                  unsigned long long& kk, unsigned long long& wops, int lane) {
+    if (w <= 1) cq_tail2<1>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+    else if (w <= 2) cq_tail2<2>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+    else if (w <= 4) cq_tail2<4>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+    else if (w <= 6) cq_tail2<6>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+    else if (w <= 8) cq_tail2<8>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+    else if (w <= 10) cq_tail2<10>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+    else if (w <= 16) cq_tail2<16>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
     else {
         // wide rows (out-degree > 512): C_i's words are recomputed from shared
         // memory instead of held in registers
@@ -217,6 +219,7 @@ __device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint3
             for (int q = 0; q < w; q++) {
                 uint32_t bits = C[q] & ri[q];
                 km1 += (unsigned)__popc(bits);
+                wops += (unsigned long long)(__popc(bits) + 1) * (unsigned)w;
                 while (bits) {
                     const int j = 32 * q + __ffs(bits) - 1;
                     bits &= bits - 1u;
@@ -234,7 +237,7 @@ __device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint3
 // and km1 (k_hi-1 cliques, used when k_lo < k_hi); smaller sizes go to wcnt.
 template <bool DONATE>
 __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_pos, int r, int d, int& cached_root,
-                        unsigned long long& unit_sum, unsigned long long& km1, int lane) {
+                        unsigned long long& unit_sum, unsigned long long& km1, unsigned long long& wops, int lane) {
     if (d < a.k_lo - 1 || d <= 0) return true;
     const int w = (d + 31) >> 5;
     const int ws = w | 1;
@@ -283,11 +286,12 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                     int c = 0;
                     for (int q = 0; q < w; q++) c += __popc(Cs[q] & row[q]);
                     sum += (unsigned)c;
+                    wops += (unsigned)w;
                 }
                 unit_sum += sum;
             } else {
                 if (lane == 0 && K - 2 >= a.k_lo) wcnt[K - 2] += (unsigned)nchild;
-                cq_tail2_dispatch(Cs, rows, w, ws, list, nchild, km1, unit_sum, lane);
+                cq_tail2_dispatch(Cs, rows, w, ws, list, nchild, km1, unit_sum, wops, lane);
             }
             __syncwarp();
             if (s == s_base) break;
@@ -307,6 +311,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
             Cn[lane] = x;
         }
         const int c = __reduce_add_sync(GPM_FULL_MASK, (unsigned)__popc(x));
+        if (lane == 0) wops += (unsigned)w;
         if (lane == 0) {
             cur[s] = i + 1;
             if (s + 1 >= a.k_lo) wcnt[s + 1] += 1ull;

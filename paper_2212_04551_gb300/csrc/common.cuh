@@ -133,6 +133,7 @@ struct Control {
     int error;                        // GPM_* status raised on the device
     unsigned long long q_head, q_tail;
     unsigned long long donations, units_done, idle_polls;
+    unsigned long long word_ops;      // clique: 32-bit candidate-word AND+POPC operations
     int overflow;
     int pad;
 };

@@ -407,6 +407,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     st.units_done = h.units_done;
     st.donations = h.donations;
     st.idle_polls = h.idle_polls;
+    st.kernel_launches = st.grid_blocks ? (n_split > 0 ? 3 : 2) : 0;
     g->stats = st;
     if (h.error) g->mark_bytes_cleared = 0;   // an aborted walk leaves marks behind
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");

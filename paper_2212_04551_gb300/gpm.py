@@ -50,7 +50,8 @@ class gpm_config(ctypes.Structure):
 class gpm_stats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("units_done", ctypes.c_uint64),
                 ("donations", ctypes.c_uint64), ("idle_polls", ctypes.c_uint64),
-                ("grid_blocks", ctypes.c_int32), ("warps_per_block", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("word_ops", ctypes.c_uint64), ("kernel_launches", ctypes.c_int32)]
 
 
 _lib = None

@@ -224,8 +224,11 @@ def _golden(name):
         return json.load(f)
 
 
-@pytest.mark.parametrize("name", ["er516", "sbm2000"])
+@pytest.mark.parametrize("name", ["er516", "sbm2000", "rmat16", "chunglu1m"])
 def test_workload_golden(name):
+    """Full-size workloads, in the launch configuration the benchmark uses:
+    full counts where the oracle finishes, else exact per-root counts on the
+    seeded root samples stored beside them."""
     data = _golden(name)
     g = G.workload(name)
     assert g.sha256() == data["sha256"]
