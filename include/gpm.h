@@ -296,6 +296,45 @@ gpm_status gpm_batch_autotune(gpm_batch* b, int clique_k, int motif_k, int reps,
 gpm_status gpm_batch_set_config(gpm_batch* b, const gpm_config* cfg);
 gpm_status gpm_batch_get_stats(const gpm_batch* b, gpm_stats* out);
 
+/*
+ * Allocation-free motif counting.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library allocate device memory
+ * -- host applications that own every device byte through their own pool or
+ * allocator, and real-time or embedded hosts with a fixed device-memory
+ * budget where a cudaMalloc during a call is not allowed.
+ *
+ * Same result as gpm_motif_count on the same graph (counts[p] = number of
+ * connected induced k-vertex subgraphs of pattern id p), computed by the same
+ * motif kernel with work donation off.  The call allocates nothing: it calls
+ * no cudaMalloc or cudaFree and no allocating library routine; its scratch
+ * (control block, counters, validation flags, root list, pattern table) is
+ * one file-scope device array of 2,138,624 bytes that every device loading
+ * the library holds until the process exits.
+ *
+ *   indptr, indices : DEVICE pointers to the undirected CSR (conventions of
+ *                     gpm_graph_create; checked on the device); not copied.
+ *   n               : 0 <= n <= 8192 vertices; the graph must also fit the
+ *                     kernel's shared-memory state (n bytes of marks plus
+ *                     sum over l <= k-2 of l * max_degree ints, at most 12 KB
+ *                     per warp).  Larger graphs are rejected with GPM_EINVAL
+ *                     and a message naming the limit.
+ *   k               : 3 <= k <= 7.
+ *   counts          : HOST array of counts_len uint64 (>= number of patterns).
+ *   stream          : cudaStream_t to run on (NULL = legacy default stream);
+ *                     the call synchronises it before returning.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The host-side pattern table of each k is
+ * built once per process in host memory.  Every call on a device shares the
+ * one scratch array, which keeps the last call's contents (each call clears
+ * what must start at zero): calls that overlap on the GPU -- on different
+ * streams or from different host threads -- race and must not be made.
+ * Errors: GPM_EINVAL, GPM_ECUDA, GPM_EOVERFLOW.
+ */
+gpm_status gpm_motif_count_noalloc(const int32_t* indptr, const int32_t* indices, int32_t n, int k,
+                                   uint64_t* counts, int64_t counts_len, void* stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* gpm_last_error(void);
 

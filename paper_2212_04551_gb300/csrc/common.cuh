@@ -230,6 +230,11 @@ struct QSeq {
 
 namespace gpm {
 __global__ void k_queue_init(QSeq* q, unsigned long long cap);
+// CSR checks (graph.cu): bits of *bad: 1 indptr, 2 id range, 4 self-loop,
+// 8 order/duplicates, 16 symmetry
+__global__ void k_validate(const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices, int32_t n,
+                           int64_t nnz, int* __restrict__ bad);
+__global__ void k_indptr_monotone(const int32_t* __restrict__ indptr, int32_t n, int* __restrict__ bad);
 }
 
 __device__ __forceinline__ bool gpm_q_reserve(QSeq* q, unsigned long long cap, unsigned long long* tail,

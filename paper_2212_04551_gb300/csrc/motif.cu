@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -418,3 +419,195 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
 }
 
 }  // namespace gpm
+
+// ---------------------------------------------------------------------------
+// Allocation-free motif counting (gpm_motif_count_noalloc).
+//
+// For callers that may not allocate device memory at all -- code that runs
+// inside a host application owning every device byte through its own pool,
+// or real-time and embedded hosts with a fixed device-memory budget where a
+// cudaMalloc at call time is not allowed.  The same shared-memory-state
+// motif kernel runs with donation off; everything it needs beyond the
+// caller's graph and result buffers -- control block, pattern counters,
+// validation flags, root list, pattern table -- sits in one file-scope
+// device array of fixed size, resident on every device that loads the
+// library until the process exits.
+// ---------------------------------------------------------------------------
+namespace gpm {
+
+constexpr int NA_MAX_N = 8192;                                 // vertices
+constexpr size_t NA_CTL_OFF = 0;                               // Control
+constexpr size_t NA_CNT_OFF = 256;                             // MT_MAXPAT uint64 counters
+constexpr size_t NA_FLAG_OFF = NA_CNT_OFF + 8192;              // validation flags, max degree
+constexpr size_t NA_ROOT_OFF = NA_FLAG_OFF + 256;              // NA_MAX_N int32 roots
+constexpr size_t NA_LUT_OFF = NA_ROOT_OFF + 4 * (size_t)NA_MAX_N;
+constexpr size_t NA_LUT_BYTES = (size_t)2 << 20;               // 2^20 uint16: pattern table up to k = 7
+constexpr size_t NA_SCRATCH_BYTES = NA_LUT_OFF + NA_LUT_BYTES;  // 2,138,624 bytes
+static_assert(sizeof(Control) <= 256, "control block must fit its slot");
+static_assert(sizeof(unsigned long long) * MT_MAXPAT <= 8192, "counters must fit their slot");
+static_assert(NA_LUT_OFF % 256 == 0, "aligned table");
+
+}  // namespace gpm
+
+// The scratch.  Host code never uses this name as an address: it asks the
+// runtime for the device address (gpm_noalloc_scratch_ptr) once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[gpm::NA_SCRATCH_BYTES];
+
+namespace gpm {
+
+__global__ void k_na_prepare(const int32_t* __restrict__ indptr, int32_t n, int32_t* __restrict__ roots,
+                             int* __restrict__ maxdeg) {
+    int local = 0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        roots[v] = (int32_t)v;
+        local = max(local, indptr[v + 1] - indptr[v]);
+    }
+    for (int o = 16; o > 0; o >>= 1) local = max(local, __shfl_xor_sync(GPM_FULL_MASK, local, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxdeg, local);
+}
+
+// Device address of the scratch on the current device; looked up on the
+// first call per device (with that device current) and remembered.
+static unsigned char* noalloc_scratch_ptr() {
+    static std::mutex mu;
+    static unsigned char* ptrs[256] = {nullptr};
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 256) fail(GPM_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            fail(GPM_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        }
+        ptrs[dev] = static_cast<unsigned char*>(p);
+    }
+    return ptrs[dev];
+}
+
+static void motif_count_noalloc(const int32_t* indptr, const int32_t* indices, int32_t n, int k, uint64_t* counts,
+                                int64_t counts_len, cudaStream_t s) {
+    if (k < 3 || k > MT_MAXK) fail(GPM_EINVAL, "k out of range [3, 7] for the allocation-free path");
+    if (n < 0 || n > NA_MAX_N)
+        fail(GPM_EINVAL, "n = " + std::to_string(n) + " exceeds the allocation-free limit of " +
+                             std::to_string(NA_MAX_N) + " vertices");
+    if (!indptr || !counts) fail(GPM_EINVAL, "NULL pointer");
+    const PatternTable& tab = pattern_table(k);
+    const int npat = (int)tab.num_patterns;
+    if (counts_len < npat) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
+    if (tab.lut.size() * sizeof(uint16_t) > NA_LUT_BYTES) fail(GPM_EINVAL, "pattern table larger than its slot");
+    unsigned char* base = noalloc_scratch_ptr();
+    Control* ctl = reinterpret_cast<Control*>(base + NA_CTL_OFF);
+    unsigned long long* dcounts = reinterpret_cast<unsigned long long*>(base + NA_CNT_OFF);
+    int* flags = reinterpret_cast<int*>(base + NA_FLAG_OFF);   // [0] CSR errors, [1] max degree
+    int32_t* roots = reinterpret_cast<int32_t*>(base + NA_ROOT_OFF);
+    uint16_t* lut = reinterpret_cast<uint16_t*>(base + NA_LUT_OFF);
+
+    int dev = 0, sms = 0;
+    GPM_CUDA(cudaGetDevice(&dev));
+    GPM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+    // CSR checks and the maximum degree (every call: the scratch is shared)
+    int32_t ends[2] = {0, 0};
+    GPM_CUDA(cudaMemcpyAsync(&ends[0], indptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GPM_CUDA(cudaMemcpyAsync(&ends[1], indptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GPM_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] < 0 || (ends[1] & 1)) fail(GPM_EINVAL, "invalid indptr");
+    if (ends[1] > 0 && !indices) fail(GPM_EINVAL, "indices is NULL");
+    GPM_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+    const int blocks = std::max(1, std::min(sms * 4, (n + 255) / 256));
+    if (n > 0) {
+        k_indptr_monotone<<<blocks, 256, 0, s>>>(indptr, n, flags);
+        k_na_prepare<<<blocks, 256, 0, s>>>(indptr, n, roots, flags + 1);
+        GPM_CUDA(cudaGetLastError());
+    }
+    int hf[2] = {0, 0};
+    GPM_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    GPM_CUDA(cudaStreamSynchronize(s));
+    if (hf[0]) fail(GPM_EINVAL, "indptr is not non-decreasing");
+    if (n > 0 && ends[1] > 0) {
+        k_validate<<<std::max(1, std::min(sms * 8, (n * 32 + 255) / 256)), 256, 0, s>>>(indptr, indices, n, ends[1],
+                                                                                      flags);
+        GPM_CUDA(cudaGetLastError());
+        GPM_CUDA(cudaMemcpyAsync(hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GPM_CUDA(cudaStreamSynchronize(s));
+        if (hf[0]) fail(GPM_EINVAL, "invalid CSR (ids, self-loops, order, duplicates or symmetry)");
+    }
+    const int maxdeg = hf[1];
+
+    // the kernel's per-warp state must fit in shared memory
+    const int wpb = 8;
+    MotifParams p{};
+    long long off = 0;
+    const long long D = std::max(maxdeg, 1);
+    for (int l = 0; l <= MT_MAXK; l++) {
+        p.lvl_off[l] = off;
+        if (l >= 1 && l <= k - 2) off += (long long)l * D + 4;
+        off = (off + 3) & ~3ll;
+    }
+    p.slab_ints = std::max(off, 4ll);
+    p.mark_stride = (int)((n + 15) & ~15);
+    const long long warp_state = (long long)p.mark_stride + 4 * p.slab_ints;
+    const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
+    p.smem_warp_bytes = (int)((warp_state + 15) & ~15ll);
+    const size_t smem = base_smem + (size_t)wpb * p.smem_warp_bytes;
+    if (warp_state > 12 * 1024 || smem > 200 * 1024)
+        fail(GPM_EINVAL, "graph too large for the allocation-free path (vertices + extension arrays must fit in "
+                         "12 KB of shared memory per warp)");
+
+    GPM_CUDA(cudaMemcpyAsync(lut, tab.lut.data(), tab.lut.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+    GPM_CUDA(cudaMemsetAsync(base, 0, NA_CNT_OFF + sizeof(unsigned long long) * MT_MAXPAT, s));
+    Control h{};
+    h.pending = n;
+    GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
+
+    p.indptr = indptr;
+    p.indices = indices;
+    p.roots = roots;
+    p.n_roots = n;
+    p.n = n;
+    p.k = k;
+    p.npat = npat;
+    p.lut = lut;
+    p.ctl = ctl;
+    p.counts = dcounts;
+    p.donate = 0;
+    p.donate_min = 2;
+    p.max_idle_ns = 120000000000ull;
+    GPM_CUDA(cudaFuncSetAttribute(k_motif<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_motif<true>, wpb * 32, smem));
+    if (per_sm <= 0) fail(GPM_EINVAL, "kernel cannot be resident");
+    if (n > 0) {
+        const int grid = std::max(1, std::min(per_sm * sms, (n + wpb - 1) / wpb));
+        k_motif<true><<<grid, wpb * 32, smem, s>>>(p);
+        GPM_CUDA(cudaGetLastError());
+    }
+    unsigned long long host[MT_MAXPAT];
+    GPM_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    GPM_CUDA(cudaMemcpyAsync(host, dcounts, sizeof(unsigned long long) * npat, cudaMemcpyDeviceToHost, s));
+    GPM_CUDA(cudaStreamSynchronize(s));
+    if (h.error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
+    if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
+    if (h.overflow) fail(GPM_EOVERFLOW, "a pattern count exceeds 2^64-1");
+    for (int j = 0; j < npat; j++) counts[j] = host[j];
+}
+
+}  // namespace gpm
+
+extern "C" gpm_status gpm_motif_count_noalloc(const int32_t* indptr, const int32_t* indices, int32_t n, int k,
+                                              uint64_t* counts, int64_t counts_len, void* stream) {
+    try {
+        gpm::clear_error();
+        gpm::motif_count_noalloc(indptr, indices, n, k, counts, counts_len, reinterpret_cast<cudaStream_t>(stream));
+        return GPM_OK;
+    } catch (const gpm::Error& e) {
+        gpm::set_error(e.msg);
+        return e.status;
+    } catch (...) {
+        gpm::set_error("unexpected internal error");
+        return GPM_ECUDA;
+    }
+}

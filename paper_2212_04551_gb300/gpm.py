@@ -91,6 +91,7 @@ SIGNATURES = {
                                           ctypes.POINTER(gpm_config), ctypes.POINTER(ctypes.c_double)]),
     "gpm_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
     "gpm_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
+    "gpm_motif_count_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, _u64p, ctypes.c_int64, _vp]),
 }
 GPM_MLP_PARAMS = 4801
 
@@ -439,3 +440,14 @@ def batch_from_graphs(graph_list, stream=None) -> Batch:
     indptr = np.concatenate(ip_parts).astype(np.int32)
     indices = (np.concatenate(ix_parts) if ix_parts else np.zeros(0, dtype=np.int64)).astype(np.int32)
     return gpm_batch_create(goff.astype(np.int32), indptr, indices, stream=stream)
+
+
+def gpm_motif_count_noalloc(indptr, indices, n: int, k: int, stream=None) -> np.ndarray:
+    """Allocation-free motif counting on a graph already on the device
+    (CUDA int32 tensors); see include/gpm.h for the limits."""
+    npat = gpm_motif_num_patterns(k)
+    out = np.zeros(npat, dtype=np.uint64)
+    _check(load().gpm_motif_count_noalloc(_dev_ptr(indptr, "indptr"), _dev_ptr(indices, "indices") if
+                                          indices.numel() else None, int(n), int(k), out.ctypes.data_as(_u64p),
+                                          npat, _stream_handle(stream)), "gpm_motif_count_noalloc")
+    return out
