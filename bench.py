@@ -203,7 +203,7 @@ def timed(fn, stream):
     return out, e0.elapsed_time(e1)
 
 
-def learned_vs_plain(stream, k: int = 5, n_roots: int = 1024, epochs: int = 60, reps: int = 3) -> dict:
+def learned_vs_plain(stream, k: int = 5, n_roots: int = 512, epochs: int = 60, reps: int = 2) -> dict:
     """Learned scheduling (the MLP trained on R-MAT scale-12 graphs, seeds
     100-131, with per-root sizes measured by the plain enumerator) against the
     plain heaviest-degree-first donation scheduler, on the R-MAT scale-16 graph
@@ -229,42 +229,44 @@ def learned_vs_plain(stream, k: int = 5, n_roots: int = 1024, epochs: int = 60, 
     roots = G.sample_roots(g.n, n_roots, seed=25, exclude=~ok)
     dg = gpm.graph_from_csr(g, stream=stream)
     feats = L.features(dg, g.n)
-    warps = None
+    pred_trained = L.predict(model, feats, stream)
+    pred_untrained = L.predict(untrained, feats, stream)
     res = {}
     ref = None
     sizes = None
-    for name, scorer in (("plain", None), ("learned", model), ("untrained", untrained)):
-        if scorer is None:
-            gpm.gpm_sched_from_scores(dg, gpm.GPM_APP_MOTIF, None, roots, 0, 0)
-            plan = {"split_roots": 0, "chunks": 0}
-        else:
-            pred = L.predict(scorer, feats, stream)
-            if warps is None:
-                warps = gpm.gpm_get_stats(dg)["grid_blocks"] * gpm.gpm_get_stats(dg)["warps_per_block"] or 4864
-            plan = L.schedule(dg, gpm.GPM_APP_MOTIF, pred, roots, warps=warps, chunks=8)
-        times = []
-        for _ in range(reps):
-            (c, pr), ms = timed(lambda: gpm.gpm_count_scheduled(dg, gpm.GPM_APP_MOTIF, k, n_roots=len(roots),
-                                                                per_root=True), stream)
-            times.append(ms)
-        st = gpm.gpm_get_stats(dg)
-        if ref is None:
-            ref, sizes = c, pr
-        assert np.array_equal(c, ref), f"{name} schedule changed the counts"
-        total = int(c.sum())
-        ms = statistics.median(times)
-        res[name] = {"ms": ms, "subgraphs_per_s": total / (ms / 1000.0), "donations": int(st["donations"]),
-                     "units": int(st["units_done"]), **plan}
-        if scorer is not None:
-            p = L.predict(scorer, feats, stream).cpu().numpy()[roots]
-            from scipy.stats import spearmanr
-            res[name]["spearman_vs_measured"] = float(spearmanr(p, np.log1p(sizes.astype(np.float64))).statistic)
+    for donate in (1, 0):
+        gpm.gpm_set_config(dg, donate=donate)
+        tag = "donation" if donate else "static"
+        res[tag] = {}
+        for name, pred in (("plain", None), ("learned", pred_trained), ("untrained", pred_untrained)):
+            if pred is None:
+                gpm.gpm_sched_from_scores(dg, gpm.GPM_APP_MOTIF, None, roots, 0, 0)
+                plan = {"split_roots": 0, "chunks": 0}
+            else:
+                plan = L.schedule(dg, gpm.GPM_APP_MOTIF, pred, roots, warps=4864, chunks=8)
+            times = []
+            for _ in range(reps):
+                (c, pr), ms = timed(lambda: gpm.gpm_count_scheduled(dg, gpm.GPM_APP_MOTIF, k, n_roots=len(roots),
+                                                                    per_root=True), stream)
+                times.append(ms)
+            st = gpm.gpm_get_stats(dg)
+            if ref is None:
+                ref, sizes = c, pr
+            assert np.array_equal(c, ref), f"{name} schedule changed the counts"
+            ms = statistics.median(times)
+            res[tag][name] = {"ms": ms, "subgraphs_per_s": int(ref.sum()) / (ms / 1000.0),
+                              "donations": int(st["donations"]), "units": int(st["units_done"]), **plan}
+        res[tag]["speedup_learned_vs_plain"] = res[tag]["plain"]["ms"] / res[tag]["learned"]["ms"]
+    from scipy.stats import spearmanr
+    meas = np.log1p(sizes.astype(np.float64))
+    res["spearman_trained"] = float(spearmanr(pred_trained.cpu().numpy()[roots], meas).statistic)
+    res["spearman_untrained"] = float(spearmanr(pred_untrained.cpu().numpy()[roots], meas).statistic)
+    res["spearman_degree"] = float(spearmanr(g.degrees()[roots], meas).statistic)
     res["k"] = k
     res["roots"] = f"{len(roots)} seeded roots of rmat16 (id >= 1024, degree <= 32)"
     res["subgraphs"] = int(ref.sum())
     res["train"] = {"samples": int(X.shape[0]), "epochs": epochs, "label_s": round(t_labels, 2),
                     "train_s": round(t_train, 2), "final_mse": model.history[-1], "first_mse": model.history[0]}
-    res["speedup_learned_vs_plain"] = res["plain"]["ms"] / res["learned"]["ms"]
     dg.close()
     return res
 
@@ -275,7 +277,7 @@ def batched_vs_plain(stream, reps: int = 5) -> dict:
     form (one gpm_clique_count + one gpm_motif_count per graph)."""
     from paper_2212_04551_gb300 import gpm
     from paper_2212_04551_gb300 import graphs as G
-    gs = G.workload("ba4096")
+    gs = list(G.workload("ba4096"))
     b = gpm.batch_from_graphs(gs, stream=stream)
     best, _ = gpm.gpm_batch_autotune(b, 4, 5, reps=3)
     cc, mc = gpm.gpm_batch_count(b, 4, 5)

@@ -153,7 +153,7 @@ gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, i
  * work is split and ordered (Section 4.3.5 replaced by in-kernel donation).
  */
 typedef struct {
-    int32_t warps_per_block;   /* 1, 2, 4, 8 or 16 (0 = default 8)                     */
+    int32_t warps_per_block;   /* 1, 2, 4, 8 or 16 (0 = the most resident warps/SM)    */
     int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum)       */
     int32_t donate_min;        /* split a level only if >= this many siblings remain  */
     int32_t order;             /* GPM_ORDER_* root order of the plain scheduler         */
@@ -161,6 +161,7 @@ typedef struct {
                                /* without any progress anywhere (GPM_ETIMEOUT)         */
     int32_t donate;            /* 0 disables work donation                             */
     int32_t donate_after_us;   /* a unit is split only after it has run this long      */
+    int32_t clique_tail;       /* clique levels finished lane-parallel: 2 or 3 (0: 3 for k >= 7, else 2) */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */

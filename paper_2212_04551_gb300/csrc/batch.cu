@@ -102,13 +102,17 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     cw.hiv = reinterpret_cast<int*>(cq + L.hi);
     cw.cand = cq + L.cand;
     cw.list = reinterpret_cast<int*>(cq + L.list);
+    cw.pairs = reinterpret_cast<int*>(cq + L.pairs);
     cw.rows = cq + L.rows;
     cw.ctl = p.ctl;
-    cw.qseq = nullptr;
-    cw.qunits = nullptr;
-    cw.qcap = 0;
+    cw.ring_seq = nullptr;
+    cw.ring_ids = nullptr;
+    cw.ring_cap = 0;
+    cw.mbox = nullptr;
+    cw.mbox_stride = 0;
     cw.donate_min = 0;
     cw.donate_after_ns = 0;
+    cw.tail_levels = 0;
     // motif part
     unsigned char* mt = base + (size_t)p.cq_words * 4;
     MtWarp* W = reinterpret_cast<MtWarp*>(mt);
@@ -125,10 +129,11 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     mw.slab = slab;
     mw.lvl_off = p.lvl_off;
     mw.ctl = p.ctl;
-    mw.qseq = nullptr;
-    mw.qunits = nullptr;
-    mw.qpayload = nullptr;
-    mw.qcap = 0;
+    mw.ring_seq = nullptr;
+    mw.ring_ids = nullptr;
+    mw.ring_cap = 0;
+    mw.mbox = nullptr;
+    mw.mbox_stride = 0;
     mw.donate_min = 0;
     mw.donate_after_ns = 0;
     mw.err = &p.ctl->error;

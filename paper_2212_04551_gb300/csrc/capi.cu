@@ -215,8 +215,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         check_graph(g);
         if (!cfg) fail(GPM_EINVAL, "cfg is NULL");
         gpm_config c = *cfg;
-        if (c.warps_per_block == 0) c.warps_per_block = 8;
-        if (c.warps_per_block != 1 && c.warps_per_block != 2 && c.warps_per_block != 4 &&
+        if (c.warps_per_block != 0 && c.warps_per_block != 1 && c.warps_per_block != 2 && c.warps_per_block != 4 &&
             c.warps_per_block != 8 && c.warps_per_block != 16)
             fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 16]");
         if (c.blocks_per_sm < 0) fail(GPM_EINVAL, "blocks_per_sm < 0");
@@ -224,6 +223,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.order < GPM_ORDER_ID || c.order > GPM_ORDER_CUSTOM) fail(GPM_EINVAL, "unknown order");
         if (c.max_idle_ms <= 0) fail(GPM_EINVAL, "max_idle_ms must be positive");
         if (c.donate_after_us < 0) fail(GPM_EINVAL, "donate_after_us < 0");
+        if (c.clique_tail != 0 && c.clique_tail != 2 && c.clique_tail != 3) fail(GPM_EINVAL, "clique_tail must be 0, 2 or 3");
         g->cfg = c;
     });
 }

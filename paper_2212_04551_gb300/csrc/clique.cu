@@ -40,6 +40,8 @@
 
 namespace gpm {
 
+constexpr unsigned long long CQ_MAX_SEEDS = 65536;   // pre-split units per launch
+
 struct CliqueParams {
     const int32_t* __restrict__ off;
     const int32_t* __restrict__ adj;
@@ -52,13 +54,18 @@ struct CliqueParams {
     int maxd;
     int stride_words;    // shared-memory words per warp
     Control* ctl;
-    QSeq* qseq;
-    CliqueUnit* qunits;
-    unsigned long long qcap;
+    QSeq* ring_seq;             // idle-warp ring
+    int32_t* ring_ids;
+    unsigned long long ring_cap;
+    unsigned char* mbox;        // per-warp mailboxes
+    int mbox_stride;
+    const CliqueUnit* seeds;    // pre-split seed units
+    long long n_seeds;
     unsigned long long* per_root;   // nullable
     int donate, donate_min;
     unsigned long long donate_after_ns;
     unsigned long long max_idle_ns;
+    int tail_levels;
 };
 
 __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
@@ -90,13 +97,17 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     walk.hiv = hiv;
     walk.cand = cand;
     walk.list = list;
+    walk.pairs = reinterpret_cast<int*>(base + L.pairs);
     walk.rows = rows;
     walk.ctl = ctl;
-    walk.qseq = p.qseq;
-    walk.qunits = p.qunits;
-    walk.qcap = p.qcap;
+    walk.ring_seq = p.ring_seq;
+    walk.ring_ids = p.ring_ids;
+    walk.ring_cap = p.ring_cap;
+    walk.mbox = p.mbox;
+    walk.mbox_stride = p.mbox_stride;
     walk.donate_min = p.donate_min;
     walk.donate_after_ns = p.donate_after_ns;
+    walk.tail_levels = p.tail_levels;
 
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
     unsigned long long top_km1 = 0;   // lane-private (k_hi-1)-clique count
@@ -109,16 +120,20 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     unsigned long long idle_since = 0;
     bool aborted = false;
 
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // this warp's global id
+    MailHdr* my_box = reinterpret_cast<MailHdr*>(p.mbox + (size_t)gw * p.mbox_stride);
+    const CliqueUnit* my_unit = reinterpret_cast<const CliqueUnit*>(p.mbox + (size_t)gw * p.mbox_stride + sizeof(MailHdr));
+    bool registered = false;
+
     while (!aborted) {
-        // ---- acquire a unit: donated work first, then the next root
+        // ---- acquire a unit: pre-split seeds, then roots, then donated work
         int kind = 0;
         if (lane == 0) {
-            unsigned long long pos;
-            if (p.donate && gpm_q_claim(p.qseq, p.qcap, &ctl->q_head, &pos)) {
-                gpm_load_cg(unit, &p.qunits[pos % p.qcap]);
-                __threadfence();
-                gpm_q_release(p.qseq, p.qcap, pos);
-                kind = 2;
+            unsigned long long sd = *(volatile unsigned long long*)&ctl->next_seed;
+            if (sd < (unsigned long long)p.n_seeds) sd = atomicAdd(&ctl->next_seed, 1ull);
+            if (sd < (unsigned long long)p.n_seeds) {
+                *unit = p.seeds[sd];
+                kind = 3;
             } else {
                 unsigned long long r = *(volatile unsigned long long*)&ctl->next_root;
                 if (r < (unsigned long long)p.n_roots) r = atomicAdd(&ctl->next_root, 1ull);
@@ -128,19 +143,30 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
                     unit->lo = 0;
                     unit->hi = -1;
                     kind = 1;
+                } else if (registered && *(volatile int*)&my_box->ready) {
+                    __threadfence();
+                    gpm_load_cg(unit, my_unit);
+                    *(volatile int*)&my_box->ready = 0;
+                    kind = 2;
                 }
             }
         }
         kind = __shfl_sync(GPM_FULL_MASK, kind, 0);
         __syncwarp();
+        if (kind == 2) registered = false;
 
         if (!kind) {
-            // ---- idle: wait (bounded) for donated work or global completion
+            // ---- idle: register once for a hand-off, then wait (bounded) on
+            // this warp's own mailbox or global completion
             if (!idle) {
-                if (lane == 0) atomicAdd(&ctl->idle, 1);
                 idle = true;
                 last_pending = -1;
                 idle_since = gpm_globaltimer();
+            }
+            if (p.donate && !registered) {
+                int ok = 0;
+                if (lane == 0) ok = gpm_idle_register(p.ring_seq, p.ring_ids, p.ring_cap, &ctl->q_tail, gw) ? 1 : 0;
+                registered = __shfl_sync(GPM_FULL_MASK, ok, 0) != 0;
             }
             long long pend = 0;
             int err = 0;
@@ -160,13 +186,10 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
                 break;
             }
             polls++;
-            __nanosleep(++spin < 32 ? 256 : 2048);   // short backoff first, then longer
+            __nanosleep(++spin < 32 ? 128 : 1024);   // short backoff first, then longer
             continue;
         }
-        if (idle) {
-            if (lane == 0) atomicSub(&ctl->idle, 1);
-            idle = false;
-        }
+        idle = false;
         spin = 0;
 
         // ---- process the unit
@@ -204,9 +227,9 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
 
 // Pre-split seeds: split root j (entries [n_counter, n_counter + n_split) of
 // the root list) into `chunks` units over equal index ranges of its children,
-// placed in queue slots [j*chunks, (j+1)*chunks) and published.
+// written to seeds[j*chunks .. (j+1)*chunks).
 __global__ void k_clique_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
-                              const int32_t* __restrict__ outdeg, QSeq* qseq, CliqueUnit* qunits) {
+                              const int32_t* __restrict__ outdeg, CliqueUnit* seeds) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_split) return;
     const long long pos = n_counter + j;
@@ -219,8 +242,7 @@ __global__ void k_clique_seed(const int32_t* __restrict__ roots, long long n_cou
         u.lo = (int)((long long)d * c / chunks);
         u.hi = (int)((long long)d * (c + 1) / chunks);
         for (int z = 0; z < GPM_CLIQUE_MAX_K; z++) u.path[z] = 0;
-        qunits[slot] = u;
-        qseq[slot].seq = (unsigned long long)slot + 1;
+        seeds[slot] = u;
     }
 }
 
@@ -251,14 +273,13 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
     }
     if (n_counter < 0 || n_counter > n_roots) n_counter = n_roots;
     const int n_split = (int)(n_roots - n_counter);
-    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > CQ_QUEUE_CAP / 2))
-        fail(GPM_EINVAL, "pre-split schedule does not fit the work queue");
+    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > CQ_MAX_SEEDS))
+        fail(GPM_EINVAL, "pre-split schedule has too many units");
     const unsigned long long n_seed = n_split > 0 ? (unsigned long long)n_split * split_chunks : 0ull;
     g->scratch_small.ensure(sizeof(Control));
     Control* ctl = g->scratch_small.as<Control>();
     Control h{};
     h.pending = n_counter + (long long)n_seed;
-    h.q_tail = n_seed;
     GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
     if (d_per_root && n_roots > 0)
         GPM_CUDA(cudaMemsetAsync(d_per_root, 0, sizeof(unsigned long long) * n_roots, s));
@@ -289,7 +310,8 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         p.ws = p.wmax | 1;
         const CqLayout L = cq_layout(p.maxd, p.wmax, p.ws);
         p.stride_words = L.total;
-        int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block : 8;
+        int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block
+                                              : best_warps_per_block((const void*)k_clique, (size_t)L.total * 4, 0);
         size_t smem = (size_t)wpb * L.total * 4;
         while (smem > 227 * 1024 && wpb > 1) {
             wpb /= 2;
@@ -298,19 +320,34 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         if (smem > 227 * 1024) fail(GPM_ENOTIMPL, "clique bitmap does not fit in shared memory");
         GPM_CUDA(cudaFuncSetAttribute(k_clique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         Grid gr = plan_grid(g, (const void*)k_clique, wpb, smem);
-        g->scratch_queue.ensure((sizeof(QSeq) + sizeof(CliqueUnit)) * CQ_QUEUE_CAP);
-        p.qseq = g->scratch_queue.as<QSeq>();
-        p.qunits = reinterpret_cast<CliqueUnit*>(p.qseq + CQ_QUEUE_CAP);
-        p.qcap = CQ_QUEUE_CAP;
-        k_queue_init<<<16, 256, 0, s>>>(p.qseq, CQ_QUEUE_CAP);
+        // idle ring (capacity: a power of two >= every warp), mailboxes, seeds
+        unsigned long long cap = 1;
+        while (cap < (unsigned long long)gr.total_warps()) cap <<= 1;
+        const size_t stride = (sizeof(MailHdr) + sizeof(CliqueUnit) + 127) & ~size_t(127);
+        const size_t ring_bytes = (sizeof(QSeq) + sizeof(int32_t)) * cap;
+        const size_t mbox_bytes = stride * (size_t)gr.total_warps();
+        const size_t seed_bytes = sizeof(CliqueUnit) * std::max<unsigned long long>(n_seed, 1);
+        g->scratch_queue.ensure(ring_bytes + mbox_bytes + seed_bytes + 256);
+        unsigned char* qb = g->scratch_queue.as<unsigned char>();
+        p.ring_seq = reinterpret_cast<QSeq*>(qb);
+        p.ring_ids = reinterpret_cast<int32_t*>(qb + sizeof(QSeq) * cap);
+        p.ring_cap = cap;
+        p.mbox = qb + ((ring_bytes + 127) & ~size_t(127));
+        p.mbox_stride = (int)stride;
+        CliqueUnit* seeds = reinterpret_cast<CliqueUnit*>(p.mbox + mbox_bytes);
+        p.seeds = seeds;
+        p.n_seeds = (long long)n_seed;
+        k_queue_init<<<16, 256, 0, s>>>(p.ring_seq, cap);
+        GPM_CUDA(cudaMemsetAsync(p.mbox, 0, mbox_bytes, s));
         if (n_split > 0)
             k_clique_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks,
-                                                               p.outdeg, p.qseq, p.qunits);
+                                                               p.outdeg, seeds);
         p.ctl = ctl;
         p.per_root = d_per_root;
         p.donate = g->cfg.donate;
         p.donate_min = std::max(2, g->cfg.donate_min);
         p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
+        p.tail_levels = g->cfg.clique_tail;
         p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
         GPM_CUDA(cudaEventRecord(g->ev0, s));
         k_clique<<<gr.blocks, wpb * 32, smem, s>>>(p);

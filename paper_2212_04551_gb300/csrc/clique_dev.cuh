@@ -30,7 +30,8 @@ namespace gpm {
 
 constexpr int CQ_LEVELS = GPM_CLIQUE_MAX_K + 1;
 constexpr int CQ_MAX_OUTDEG = 1024;          // bitmap rows of at most 32 words
-constexpr unsigned long long CQ_QUEUE_CAP = 8192;
+
+constexpr int CQ_PAIR_FLUSH = 128;            // run the pair batch once it holds this many
 
 struct CliqueUnit {
     int32_t root_pos;                   // index into the root list
@@ -44,7 +45,7 @@ static_assert(sizeof(CliqueUnit) % 4 == 0, "unit must be word-sized");
 
 // shared-memory layout of one warp, in 32-bit words
 struct CqLayout {
-    int wcnt, unit, cur, hi, cand, list, rows, total;
+    int wcnt, unit, cur, hi, cand, list, pairs, rows, total;
 };
 
 __host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, int ws) {
@@ -55,7 +56,8 @@ __host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, int ws) {
     L.hi = L.cur + CQ_LEVELS;
     L.cand = L.hi + CQ_LEVELS;                         // CQ_LEVELS x wmax candidate bitmaps
     L.list = L.cand + CQ_LEVELS * wmax;                // 32*wmax ints: N+(r), later the child list
-    L.rows = L.list + 32 * wmax;                       // maxd x ws bit rows
+    L.pairs = L.list + 32 * wmax;                      // pair batch of the three-level tail
+    L.rows = L.pairs + CQ_PAIR_FLUSH + 32 * wmax;      // maxd x ws bit rows
     L.total = L.rows + maxd * ws;
     L.total = (L.total + 3) & ~3;                      // keep every warp 16-byte aligned
     return L;
@@ -132,14 +134,18 @@ struct CliqueWalk {
     int* hiv;
     uint32_t* cand;
     int* list;
+    int* pairs;
     uint32_t* rows;
-    // donation (DONATE only)
+    // donation (DONATE only): ring of idle warp ids and the warps' mailboxes
     Control* ctl;
-    QSeq* qseq;
-    CliqueUnit* qunits;
-    unsigned long long qcap;
+    QSeq* ring_seq;
+    int32_t* ring_ids;
+    unsigned long long ring_cap;
+    unsigned char* mbox;        // mailbox of warp w at mbox + w * mbox_stride: MailHdr, CliqueUnit
+    int mbox_stride;
     int donate_min;
     unsigned long long donate_after_ns;   // a unit splits only after running this long
+    int tail_levels;                      // 2 or 3 (0: 3)
 };
 
 // Compact the children of a node (set bits of C in [from, to)) into list[];
@@ -155,6 +161,45 @@ __device__ __forceinline__ int cq_compact(const uint32_t* C, int w, int from, in
     }
     __syncwarp();
     return n;
+}
+
+// sum over the set bits l of x (W >= w words, in registers) of
+// popc(x & row_l): the cliques one level below the node whose candidates are
+// x.  Two rows are loaded per step so that each lane has two independent
+// shared-memory loads in flight.
+template <int W>
+__device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const uint32_t* rows, int w, int ws) {
+    unsigned acc = 0;
+    for (int q = 0; q < w; q++) {
+        // word q of x without dynamic register indexing
+        uint32_t bits = 0;
+#pragma unroll
+        for (int z = 0; z < W; z++)
+            if (z == q) bits = x[z];
+        while (bits) {
+            const int l1 = 32 * q + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const uint32_t* r1 = rows + l1 * ws;
+            if (bits) {
+                const int l2 = 32 * q + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const uint32_t* r2 = rows + l2 * ws;
+                uint32_t a[W], b[W];
+#pragma unroll
+                for (int z = 0; z < W; z++) {
+                    a[z] = z < w ? r1[z] : 0u;
+                    b[z] = z < w ? r2[z] : 0u;
+                }
+#pragma unroll
+                for (int z = 0; z < W; z++) acc += __popc(x[z] & a[z]) + __popc(x[z] & b[z]);
+            } else {
+#pragma unroll
+                for (int z = 0; z < W; z++)
+                    if (z < w) acc += __popc(x[z] & r1[z]);
+            }
+        }
+    }
+    return acc;
 }
 
 // The last two levels below a node of size k-3 with candidates C, children
@@ -180,23 +225,7 @@ __device__ __forceinline__ void cq_tail2(const uint32_t* C, const uint32_t* rows
         }
         km1 += (unsigned)g;
         wops += (unsigned long long)(g + 1) * (unsigned)w;
-        unsigned acc = 0;
-        for (int q = 0; q < w; q++) {
-            // word q of C_i without dynamic register indexing
-            uint32_t bits = 0;
-#pragma unroll
-            for (int z = 0; z < W; z++)
-                if (z == q) bits = ci[z];
-            while (bits) {
-                const int j = 32 * q + __ffs(bits) - 1;
-                bits &= bits - 1u;
-                const uint32_t* rj = rows + j * ws;
-#pragma unroll
-                for (int z = 0; z < W; z++)
-                    if (z < w) acc += __popc(ci[z] & rj[z]);
-            }
-        }
-        kk += acc;
+        kk += cq_sum_rows<W>(ci, rows, w, ws);
     }
 }
 
@@ -230,6 +259,93 @@ __device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint3
             kk += acc;
         }
     }
+}
+
+// Pairs (i, j) -- a child i of a node of size k-4 and a child j of i -- in
+// pairs[0..np), packed (i << 16) | j.  Lane t takes pairs t, t+32, ...:
+// C_ij = C & row_i & row_j (one 3-input AND per word; its popcount is the
+// (k-1)-cliques through (i, j)), then popc(C_ij & row_l) for every l in C_ij
+// adds the k-cliques: aggregate_counter on every (k-1)-clique.
+template <int W>
+__device__ __forceinline__ void cq_pairs_run(const uint32_t (&c)[W], const uint32_t* rows, int w, int ws,
+                                             const int* pairs, int np, unsigned long long& km1,
+                                             unsigned long long& kk, unsigned long long& wops, int lane) {
+    for (int t = lane; t < np; t += 32) {
+        const int pr = pairs[t];
+        const uint32_t* ri = rows + (pr >> 16) * ws;
+        const uint32_t* rj = rows + (pr & 0xffff) * ws;
+        uint32_t cij[W];
+        int g = 0;
+#pragma unroll
+        for (int z = 0; z < W; z++) {
+            cij[z] = z < w ? (c[z] & ri[z] & rj[z]) : 0u;
+            g += __popc(cij[z]);
+        }
+        km1 += (unsigned)g;
+        wops += (unsigned long long)(g + 1) * (unsigned)w;
+        kk += cq_sum_rows<W>(cij, rows, w, ws);
+    }
+}
+
+// The last three levels below a node of size k-4 with candidates C and
+// children in [from, to): its children i are walked in order (warp-uniform);
+// the grandchildren j of each (bits of C & row_i) are appended to a shared
+// pair batch with ballot compaction, and the batch is run lane-parallel
+// (cq_pairs_run) whenever it holds CQ_PAIR_FLUSH pairs -- every lane gets a
+// pair, however few children each node has.  Uniform counts: n3 children
+// (size k-3), n2 pairs (size k-2).
+template <int W>
+__device__ __forceinline__ void cq_tail3(const uint32_t* C, const uint32_t* rows, int w, int ws, int from, int to,
+                                         int* pairs, unsigned long long& n3, unsigned long long& n2,
+                                         unsigned long long& km1, unsigned long long& kk, unsigned long long& wops,
+                                         int lane) {
+    uint32_t c[W];
+#pragma unroll
+    for (int z = 0; z < W; z++) c[z] = z < w ? C[z] : 0u;
+    int np = 0;
+    for (int q = 0; q < w; q++) {
+        uint32_t word = C[q] & range_mask(q, from, to);
+        while (word) {
+            const int i = 32 * q + __ffs(word) - 1;
+            word &= word - 1u;
+            n3 += 1;
+            const uint32_t* ri = rows + i * ws;
+            for (int q2 = 0; q2 < w; q2++) {
+                const uint32_t ciw = C[q2] & ri[q2];
+                const bool bit = (ciw >> lane) & 1u;
+                const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
+                if (bit) pairs[np + __popc(bal & gpm_lanemask_lt())] = (i << 16) | (32 * q2 + lane);
+                np += __popc(bal);
+            }
+            if (lane == 0) wops += (unsigned)w;
+            if (np >= CQ_PAIR_FLUSH) {
+                __syncwarp();
+                n2 += (unsigned)np;
+                cq_pairs_run<W>(c, rows, w, ws, pairs, np, km1, kk, wops, lane);
+                __syncwarp();
+                np = 0;
+            }
+        }
+    }
+    if (np) {
+        __syncwarp();
+        n2 += (unsigned)np;
+        cq_pairs_run<W>(c, rows, w, ws, pairs, np, km1, kk, wops, lane);
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void cq_tail3_dispatch(const uint32_t* C, const uint32_t* rows, int w, int ws, int from,
+                                                  int to, int* pairs, unsigned long long& n3, unsigned long long& n2,
+                                                  unsigned long long& km1, unsigned long long& kk,
+                                                  unsigned long long& wops, int lane) {
+    if (w <= 1) cq_tail3<1>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 2) cq_tail3<2>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 4) cq_tail3<4>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 6) cq_tail3<6>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 8) cq_tail3<8>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 10) cq_tail3<10>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else cq_tail3<16>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
 }
 
 // Walk one unit (root r = roots[root_pos], d = |N+(r)|).  Returns false if it
@@ -269,13 +385,28 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         hiv[s] = unit->hi < 0 ? d : unit->hi;
     }
     __syncwarp();
-    // nodes of size `tail` are finished by the lane-parallel tail
-    const int tail = K >= 4 ? K - 3 : 1;
+    // nodes of size `tail` are finished by the lane-parallel tail: three
+    // levels (by default for k >= 7, where the pair batches keep every lane
+    // busy; measured slower than two levels at k = 6), else two, else one
+    const bool three = w <= 16 && K >= 5 && (a.tail_levels == 3 || (a.tail_levels == 0 && K >= 7));
+    const int tail = three ? K - 4 : (K >= 4 ? K - 3 : 1);
     const unsigned long long t_start = DONATE ? gpm_globaltimer() : 0ull;
 
     int iter = 0;
     for (;;) {
         const uint32_t* Cs = cand + s * a.wmax;
+        if (s == tail && three) {
+            unsigned long long n3 = 0, n2 = 0;
+            cq_tail3_dispatch(Cs, rows, w, ws, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
+            if (lane == 0) {
+                if (K - 3 >= a.k_lo) wcnt[K - 3] += n3;
+                if (K - 2 >= a.k_lo) wcnt[K - 2] += n2;
+            }
+            __syncwarp();
+            if (s == s_base) break;
+            s--;
+            continue;
+        }
         if (s == tail) {
             const int nchild = cq_compact(Cs, w, cur[s], hiv[s], list, lane);
             if (K == 3) {
@@ -333,10 +464,9 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
             if (lane == 0) {
                 err = *(volatile int*)&ctl->error;
                 if (gpm_globaltimer() - t_start > a.donate_after_ns) {
-                    const int idl = *(volatile int*)&ctl->idle;
                     const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
                     const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
-                    want = idl > 0 && (long long)(qt - qh) < (long long)idl;
+                    want = qt > qh;   // a registered idle warp is waiting
                 }
             }
             err = __shfl_sync(GPM_FULL_MASK, err, 0);
@@ -364,9 +494,10 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                     }
                     if (mid < 0) break;
                     if (lane == 0) {
-                        unsigned long long pos;
-                        if (gpm_q_reserve(a.qseq, a.qcap, &ctl->q_tail, &pos)) {
-                            CliqueUnit* dst = &a.qunits[pos % a.qcap];
+                        int wid;
+                        if (gpm_idle_claim(a.ring_seq, a.ring_ids, a.ring_cap, &ctl->q_head, &wid)) {
+                            unsigned char* box = a.mbox + (size_t)wid * a.mbox_stride;
+                            CliqueUnit* dst = reinterpret_cast<CliqueUnit*>(box + sizeof(MailHdr));
                             CliqueUnit u;
                             u.root_pos = root_pos;
                             u.depth = depth + (t - s_base);
@@ -378,7 +509,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                             *dst = u;
                             atomicAdd((unsigned long long*)&ctl->pending, 1ull);
                             __threadfence();
-                            gpm_q_publish(a.qseq, a.qcap, pos);
+                            atomicExch(&reinterpret_cast<MailHdr*>(box)->ready, 1);
                             atomicAdd(&ctl->donations, 1ull);
                             hiv[t] = mid;
                         }

@@ -134,6 +134,7 @@ struct Control {
     unsigned long long q_head, q_tail;
     unsigned long long donations, units_done, idle_polls;
     unsigned long long word_ops;      // clique: 32-bit candidate-word AND+POPC operations
+    unsigned long long next_seed;     // next pre-split seed unit
     int overflow;
     int pad;
 };
@@ -187,6 +188,8 @@ void order_by_score(gpm_graph* g, const float* d_score, const int32_t* d_roots, 
 // helpers
 int resident_blocks(const void* kernel, int threads, size_t smem);
 Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block);
+// warps per block (16, 8, 4, 2 or 1) that keeps the most warps resident per SM
+int best_warps_per_block(const void* kernel, size_t smem_per_warp, size_t smem_fixed);
 gpm_config default_config();
 
 }  // namespace gpm
@@ -290,6 +293,39 @@ __device__ __forceinline__ bool gpm_q_claim(QSeq* q, unsigned long long cap, uns
 // call after every reader of the slot's data is done (and fenced)
 __device__ __forceinline__ void gpm_q_release(QSeq* q, unsigned long long cap, unsigned long long pos) {
     atomicExch(&q[pos % cap].seq, pos + cap);
+}
+
+// ------------------------------------------ direct hand-off of donated work
+//
+// An idle warp registers its global warp id in a ring (the sequence-numbered
+// ring above, holding ints, capacity >= every warp of the launch) and then
+// watches only its OWN mailbox flag -- no shared word is polled.  A busy warp
+// that splits its work claims one registered id from the ring, writes the
+// unit (and payload) into that warp's mailbox, fences, and raises the flag.
+// Only the few donors contend on the ring, never the many idle warps.
+struct MailHdr {
+    int ready;                 // 1: a unit is waiting in this mailbox
+    int pad[3];
+};
+
+__device__ __forceinline__ bool gpm_idle_register(QSeq* seq, int32_t* ids, unsigned long long cap,
+                                                  unsigned long long* tail, int wid) {
+    unsigned long long pos;
+    if (!gpm_q_reserve(seq, cap, tail, &pos)) return false;
+    ids[pos % cap] = wid;
+    __threadfence();
+    gpm_q_publish(seq, cap, pos);
+    return true;
+}
+
+__device__ __forceinline__ bool gpm_idle_claim(QSeq* seq, int32_t* ids, unsigned long long cap,
+                                               unsigned long long* head, int* wid) {
+    unsigned long long pos;
+    if (!gpm_q_claim(seq, cap, head, &pos)) return false;
+    *wid = __ldcg(ids + pos % cap);
+    __threadfence();
+    gpm_q_release(seq, cap, pos);
+    return true;
 }
 
 // word-wise L2 copy of a published POD record

@@ -372,13 +372,14 @@ const int32_t* ensure_id_order(gpm_graph* g) {
 
 gpm_config default_config() {
     gpm_config c;
-    c.warps_per_block = 8;
+    c.warps_per_block = 0;   // automatic: the most resident warps per SM
     c.blocks_per_sm = 0;
     c.donate_min = 4;
     c.order = GPM_ORDER_DEGREE_DESC;
     c.max_idle_ms = 120000;
     c.donate = 1;
     c.donate_after_us = 50;
+    c.clique_tail = 0;
     return c;
 }
 
@@ -476,6 +477,23 @@ int resident_blocks(const void* kernel, int threads, size_t smem) {
     check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem),
                "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     return nb;
+}
+
+int best_warps_per_block(const void* kernel, size_t smem_per_warp, size_t smem_fixed) {
+    int best = 8, best_warps = -1;
+    for (int wpb : {16, 8, 4, 2, 1}) {
+        const size_t smem = smem_fixed + smem_per_warp * wpb;
+        if (smem > 227 * 1024) continue;
+        if (smem > 48 * 1024)
+            check_cuda(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "cudaFuncSetAttribute");
+        const int per_sm = resident_blocks(kernel, wpb * 32, smem);
+        if (per_sm * wpb > best_warps) {
+            best_warps = per_sm * wpb;
+            best = wpb;
+        }
+    }
+    return best;
 }
 
 Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block) {

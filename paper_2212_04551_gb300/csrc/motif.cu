@@ -19,7 +19,7 @@
 
 namespace gpm {
 
-constexpr unsigned long long MT_QUEUE_CAP = 4096;
+constexpr unsigned long long MT_MAX_SEEDS = 65536;   // pre-split units per launch
 
 struct MotifParams {
     const int32_t* __restrict__ indptr;
@@ -31,10 +31,13 @@ struct MotifParams {
     int npat;
     const uint16_t* __restrict__ lut;
     Control* ctl;
-    QSeq* qseq;
-    MotifUnit* qunits;
-    int32_t* qpayload;          // MT_LIST ints per slot
-    unsigned long long qcap;
+    QSeq* ring_seq;             // idle-warp ring
+    int32_t* ring_ids;
+    unsigned long long ring_cap;
+    unsigned char* mbox;        // per-warp mailboxes
+    int mbox_stride;
+    const MotifUnit* seeds;     // pre-split seed units
+    long long n_seeds;
     unsigned long long* per_root;
     unsigned char* marks;       // n bytes per warp (HBM variant)
     int32_t* slab;              // slab_ints per warp (HBM variant)
@@ -68,10 +71,11 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
     a.mbase = 0;
     a.lvl_off = p.lvl_off;
     a.ctl = ctl;
-    a.qseq = p.qseq;
-    a.qunits = p.qunits;
-    a.qpayload = p.qpayload;
-    a.qcap = p.qcap;
+    a.ring_seq = p.ring_seq;
+    a.ring_ids = p.ring_ids;
+    a.ring_cap = p.ring_cap;
+    a.mbox = p.mbox;
+    a.mbox_stride = p.mbox_stride;
     a.donate_min = p.donate_min;
     a.donate_after_ns = p.donate_after_ns;
     a.err = &ctl->error;
@@ -97,14 +101,18 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
     unsigned long long idle_since = 0;
     bool aborted = false;
 
+    unsigned char* my_box = p.mbox ? p.mbox + (size_t)gw * p.mbox_stride : nullptr;
+    bool registered = false;
+
     while (!aborted) {
+        // ---- acquire a unit: pre-split seeds, then roots, then donated work
         int kind = 0;
         if (lane == 0) {
-            unsigned long long pos;
-            if (p.donate && gpm_q_claim(p.qseq, p.qcap, &ctl->q_head, &pos)) {
-                gpm_load_cg(&W->unit, &p.qunits[pos % p.qcap]);
-                kind = 2;
-                W->qpos = pos;
+            unsigned long long sd = *(volatile unsigned long long*)&ctl->next_seed;
+            if (sd < (unsigned long long)p.n_seeds) sd = atomicAdd(&ctl->next_seed, 1ull);
+            if (sd < (unsigned long long)p.n_seeds) {
+                W->unit = p.seeds[sd];
+                kind = 3;
             } else {
                 unsigned long long r = *(volatile unsigned long long*)&ctl->next_root;
                 if (r < (unsigned long long)p.n_roots) r = atomicAdd(&ctl->next_root, 1ull);
@@ -113,18 +121,29 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                     W->unit.depth = 1;
                     W->unit.sub[0] = p.roots[r];
                     kind = 1;
+                } else if (registered && *(volatile int*)&reinterpret_cast<MailHdr*>(my_box)->ready) {
+                    __threadfence();
+                    gpm_load_cg(&W->unit, reinterpret_cast<const MotifUnit*>(my_box + sizeof(MailHdr)));
+                    kind = 2;
                 }
             }
         }
         kind = __shfl_sync(GPM_FULL_MASK, kind, 0);
         __syncwarp();
+        if (kind == 2) registered = false;
 
         if (!kind) {
+            // ---- idle: register once for a hand-off, then wait (bounded) on
+            // this warp's own mailbox or global completion
             if (!idle) {
-                if (lane == 0) atomicAdd(&ctl->idle, 1);
                 idle = true;
                 last_pending = -1;
                 idle_since = gpm_globaltimer();
+            }
+            if (p.donate && !registered) {
+                int ok = 0;
+                if (lane == 0) ok = gpm_idle_register(p.ring_seq, p.ring_ids, p.ring_cap, &ctl->q_tail, (int)gw) ? 1 : 0;
+                registered = __shfl_sync(GPM_FULL_MASK, ok, 0) != 0;
             }
             long long pend = 0;
             int err = 0;
@@ -144,13 +163,10 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                 break;
             }
             polls++;
-            __nanosleep(++spin < 32 ? 256 : 2048);   // short backoff first, then longer
+            __nanosleep(++spin < 32 ? 128 : 1024);   // short backoff first, then longer
             continue;
         }
-        if (idle) {
-            if (lane == 0) atomicSub(&ctl->idle, 1);
-            idle = false;
-        }
+        idle = false;
         spin = 0;
 
         // ---------------------------------------------------- set up the unit
@@ -174,21 +190,20 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
             // pre-split seed: the list is a suffix of the root's adjacency
             unit_ext = indices + W->unit.list_off;
             if (lane == 0) {
-                gpm_q_release(p.qseq, p.qcap, W->qpos);
                 W->len[pdepth] = W->unit.len;
                 W->cur[pdepth] = 0;
                 W->hi[pdepth] = W->unit.child_hi;
             }
         } else {
+            // donated: copy the list out of this warp's mailbox, then free it
             int32_t* dst = a.slab + p.lvl_off[pdepth];
-            const long long slot = (long long)(W->qpos % p.qcap);
-            const int32_t* src = p.qpayload + slot * MT_LIST;
+            const int32_t* src = reinterpret_cast<const int32_t*>(my_box + MT_PAYLOAD_OFF);
             const int len = W->unit.len;
             for (int t = lane; t < len; t += 32) dst[t] = __ldcg(src + t);
             __threadfence();
             __syncwarp();
             if (lane == 0) {
-                gpm_q_release(p.qseq, p.qcap, W->qpos);
+                *(volatile int*)&reinterpret_cast<MailHdr*>(my_box)->ready = 0;
                 W->len[pdepth] = len;
                 W->cur[pdepth] = 0;
                 W->hi[pdepth] = W->unit.child_hi;
@@ -233,7 +248,7 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
 // its first child on, by reference into the adjacency array.
 __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
                              const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
-                             QSeq* qseq, MotifUnit* qunits) {
+                             MotifUnit* seeds) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_split) return;
     const long long pos = n_counter + j;
@@ -255,8 +270,7 @@ __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_coun
         u.child_hi = z - a;
         for (int q = 0; q < MT_MAXK; q++) u.sub[q] = q == 0 ? r : -1;
         u.list_off = lo + a;
-        qunits[slot] = u;
-        qseq[slot].seq = (unsigned long long)slot + 1;
+        seeds[slot] = u;
     }
 }
 
@@ -273,8 +287,8 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     }
     if (n_counter < 0 || n_counter > n_roots) n_counter = n_roots;
     const int n_split = (int)(n_roots - n_counter);
-    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > MT_QUEUE_CAP / 2))
-        fail(GPM_EINVAL, "pre-split schedule does not fit the work queue");
+    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > MT_MAX_SEEDS))
+        fail(GPM_EINVAL, "pre-split schedule has too many units");
     const unsigned long long n_seed = n_split > 0 ? (unsigned long long)n_split * split_chunks : 0ull;
     gpm_stats st{};
     std::vector<unsigned long long> host(npat, 0);
@@ -313,7 +327,6 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     }
 
     const uint16_t* lut = device_lut(k);
-    const int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block : 8;
 
     MotifParams p{};
     p.indptr = g->indptr.as<int32_t>();
@@ -335,11 +348,17 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.slab_ints = std::max(off, 4ll);
 
     // per-warp state in shared memory when it is small (marks + arrays)
-    const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
     p.mark_stride = (int)((g->n + 15) & ~15);
     const long long warp_state = (long long)p.mark_stride + 4 * p.slab_ints;
-    const bool smem_state = warp_state <= 12 * 1024 && base_smem + (size_t)wpb * warp_state <= 200 * 1024;
     p.smem_warp_bytes = (int)((warp_state + 15) & ~15ll);
+    const size_t fixed_smem = sizeof(unsigned long long) * MT_MAXPAT + 16;
+    const bool smem_state = warp_state <= 12 * 1024 && fixed_smem + 8 * (sizeof(MtWarp) + warp_state) <= 200 * 1024;
+    const size_t per_warp = sizeof(MtWarp) + (smem_state ? (size_t)p.smem_warp_bytes : 0);
+    const int wpb = g->cfg.warps_per_block > 0
+                        ? g->cfg.warps_per_block
+                        : best_warps_per_block(smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>,
+                                               per_warp, fixed_smem);
+    const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
     const size_t smem = base_smem + (smem_state ? (size_t)wpb * p.smem_warp_bytes : 0);
     const void* kfun = smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>;
     GPM_CUDA(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -365,25 +384,36 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.counts = reinterpret_cast<unsigned long long*>(ctl + 1);
     Control h{};
     h.pending = n_counter + (long long)n_seed;
-    h.q_tail = n_seed;
     GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
     GPM_CUDA(cudaMemsetAsync(p.counts, 0, sizeof(unsigned long long) * MT_MAXPAT, s));
     if (d_per_root && n_roots > 0)
         GPM_CUDA(cudaMemsetAsync(d_per_root, 0, sizeof(unsigned long long) * n_roots, s));
 
-    const size_t qbytes = (sizeof(QSeq) + sizeof(MotifUnit) + sizeof(int32_t) * MT_LIST) * MT_QUEUE_CAP;
-    g->scratch_queue.ensure(qbytes);
-    p.qseq = g->scratch_queue.as<QSeq>();
-    p.qunits = reinterpret_cast<MotifUnit*>(p.qseq + MT_QUEUE_CAP);
-    p.qpayload = reinterpret_cast<int32_t*>(p.qunits + MT_QUEUE_CAP);
-    p.qcap = MT_QUEUE_CAP;
-    k_queue_init<<<16, 256, 0, s>>>(p.qseq, MT_QUEUE_CAP);
+    // idle ring (capacity: a power of two >= every warp), mailboxes, seeds
+    p.donate = g->cfg.donate;
+    unsigned long long cap = 1;
+    while (cap < (unsigned long long)nw) cap <<= 1;
+    const size_t stride = (MT_PAYLOAD_OFF + sizeof(int32_t) * MT_LIST + 127) & ~size_t(127);
+    const size_t ring_bytes = (sizeof(QSeq) + sizeof(int32_t)) * cap;
+    const size_t mbox_bytes = p.donate ? stride * (size_t)nw : 0;
+    const size_t seed_bytes = sizeof(MotifUnit) * std::max<unsigned long long>(n_seed, 1);
+    g->scratch_queue.ensure(ring_bytes + mbox_bytes + seed_bytes + 256);
+    unsigned char* qb = g->scratch_queue.as<unsigned char>();
+    p.ring_seq = reinterpret_cast<QSeq*>(qb);
+    p.ring_ids = reinterpret_cast<int32_t*>(qb + sizeof(QSeq) * cap);
+    p.ring_cap = cap;
+    p.mbox = p.donate ? qb + ((ring_bytes + 127) & ~size_t(127)) : nullptr;
+    p.mbox_stride = (int)stride;
+    MotifUnit* seeds = reinterpret_cast<MotifUnit*>(qb + ((ring_bytes + 127) & ~size_t(127)) + mbox_bytes);
+    p.seeds = seeds;
+    p.n_seeds = (long long)n_seed;
+    k_queue_init<<<16, 256, 0, s>>>(p.ring_seq, cap);
+    if (mbox_bytes) GPM_CUDA(cudaMemsetAsync(p.mbox, 0, mbox_bytes, s));
     if (n_split > 0)
         k_motif_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks, p.indptr,
-                                                          p.indices, p.qseq, p.qunits);
+                                                          p.indices, seeds);
     p.ctl = ctl;
     p.per_root = d_per_root;
-    p.donate = g->cfg.donate;
     p.donate_min = std::max(2, g->cfg.donate_min);
     p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
     p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;

@@ -33,6 +33,7 @@ namespace gpm {
 constexpr int MT_MAXK = GPM_MOTIF_MAX_K;
 constexpr int MT_LIST = 1024;                  // entries carried by one donated unit
 constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns
+constexpr int MT_PAYLOAD_OFF = 64;             // payload offset inside a mailbox (after MailHdr + MotifUnit)
 
 struct MotifUnit {
     int32_t root_pos;
@@ -65,12 +66,15 @@ struct MotifWalk {
     int mbase;
     int32_t* slab;              // this warp's extension arrays
     const long long* lvl_off;   // start of ext_l inside the slab (k-1 entries used)
-    // donation (DONATE only)
+    // donation (DONATE only): ring of idle warp ids and the warps' mailboxes
+    // (mailbox of warp w at mbox + w * mbox_stride: MailHdr, MotifUnit, then
+    // MT_LIST payload ints at MT_PAYLOAD_OFF)
     Control* ctl;
-    QSeq* qseq;
-    MotifUnit* qunits;
-    int32_t* qpayload;
-    unsigned long long qcap;
+    QSeq* ring_seq;
+    int32_t* ring_ids;
+    unsigned long long ring_cap;
+    unsigned char* mbox;
+    int mbox_stride;
     int donate_min;
     unsigned long long donate_after_ns;   // a unit splits only after running this long
     int* err;                   // device error flag
@@ -102,11 +106,30 @@ __device__ __forceinline__ void mt_count_leaves(Sink& sink, bool active, int pid
     }
 }
 
+// First position in the sorted N(v) holding a vertex above `root`.  Sets
+// rooted at `root` hold no smaller vertex, so neither their marks nor their
+// extensions ever look below it: every adjacency scan starts here.  Short
+// lists are scanned whole (a search would cost more than it skips).
+__device__ __forceinline__ int mt_above(const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+                                        int v, int root) {
+    int lo = indptr[v], hi = indptr[v + 1];
+    if (hi - lo <= 64) return lo;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (indices[mid] <= root) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 // Marks and traversal codes of a unit's prefix tr[0..pdepth-1] (W->sub).
+// Vertices below the root are never marked (see mt_above); tr[j] itself is
+// above the root for j >= 1, and the root's own mark is never read.
 __device__ __forceinline__ void mt_setup_prefix(const MotifWalk& a, MtWarp* W, int pdepth, int lane) {
+    const int root = W->sub[0];
     for (int j = 0; j < pdepth; j++) {
         const int v = W->sub[j];
-        for (int t = a.indptr[v] + lane; t < a.indptr[v + 1]; t += 32) a.mk[a.indices[t] - a.mbase] |= (unsigned char)(1u << j);
+        for (int t = mt_above(a.indptr, a.indices, v, root) + lane; t < a.indptr[v + 1]; t += 32)
+            a.mk[a.indices[t] - a.mbase] |= (unsigned char)(1u << j);
         __syncwarp();
     }
     if (lane < pdepth) a.mk[W->sub[lane] - a.mbase] |= 0x80;
@@ -122,9 +145,11 @@ __device__ __forceinline__ void mt_setup_prefix(const MotifWalk& a, MtWarp* W, i
 
 // Zero the prefix marks (deeper marks were undone by the pops).
 __device__ __forceinline__ void mt_clear_prefix(const MotifWalk& a, MtWarp* W, int pdepth, int lane) {
+    const int root = W->sub[0];
     for (int j = 0; j < pdepth; j++) {
         const int v = W->sub[j];
-        for (int t = a.indptr[v] + lane; t < a.indptr[v + 1]; t += 32) a.mk[a.indices[t] - a.mbase] = 0;
+        for (int t = mt_above(a.indptr, a.indices, v, root) + lane; t < a.indptr[v + 1]; t += 32)
+            a.mk[a.indices[t] - a.mbase] = 0;
         __syncwarp();
     }
     if (lane < pdepth) a.mk[W->sub[lane] - a.mbase] = 0;
@@ -158,7 +183,7 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
             if (l == pdepth) break;
             // pop tr[l-1] (pushed at depth l-1)
             const int w = W->sub[l - 1];
-            for (int t = a.indptr[w] + lane; t < a.indptr[w + 1]; t += 32)
+            for (int t = mt_above(a.indptr, a.indices, w, root) + lane; t < a.indptr[w + 1]; t += 32)
                 a.mk[a.indices[t] - a.mbase] &= (unsigned char)~(1u << (l - 1));
             __syncwarp();
             if (lane == 0) a.mk[w - a.mbase] &= 0x7f;
@@ -171,7 +196,7 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
         if (lane == 0) W->cur[l] = c + 1;
         const int sigw = a.mk[w - a.mbase] & ((1 << l) - 1);
         const int codew = l >= 2 ? (W->code[l] | (sigw << mt_code_off(l))) : 0;
-        const int wb = a.indptr[w], we = a.indptr[w + 1];
+        const int wb = mt_above(a.indptr, a.indices, w, root), we = a.indptr[w + 1];
         const unsigned char low = (unsigned char)(0x80 | ((1u << l) - 1));
         if (l + 1 == k - 1) {
             // ---- last level: leaves of the (k-1)-set tr + w
@@ -248,10 +273,9 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
             if (lane == 0) {
                 err = *(volatile int*)&ctl->error;
                 if (gpm_globaltimer() - t_start > a.donate_after_ns) {
-                    const int idl = *(volatile int*)&ctl->idle;
                     const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
                     const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
-                    want = idl > 0 && (long long)(qt - qh) < (long long)idl;
+                    want = qt > qh;   // a registered idle warp is waiting
                 }
             }
             err = __shfl_sync(GPM_FULL_MASK, err, 0);
@@ -259,7 +283,7 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
             want = __shfl_sync(GPM_FULL_MASK, want, 0);
             if (want) {
                 // shallowest level with enough unexpanded children: give away the
-                // upper half (its list suffix travels in the slot's payload)
+                // upper half (its list suffix travels in the receiver's mailbox)
                 for (int t = pdepth; t <= l; t++) {
                     const int from = W->cur[t], to = W->hi[t], len = W->len[t];
                     const int rem = to - from;
@@ -267,14 +291,12 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
                     int start = from + (rem - rem / 2);
                     start = max(start, len - MT_LIST);
                     if (start >= to) continue;
-                    unsigned long long pos = 0;
-                    int ok = 0;
-                    if (lane == 0) ok = gpm_q_reserve(a.qseq, a.qcap, &ctl->q_tail, &pos) ? 1 : 0;
-                    ok = __shfl_sync(GPM_FULL_MASK, ok, 0);
-                    if (!ok) break;
-                    pos = __shfl_sync(GPM_FULL_MASK, pos, 0);
-                    const long long slot = (long long)(pos % a.qcap);
-                    int32_t* dst = a.qpayload + slot * MT_LIST;
+                    int wid = -1;
+                    if (lane == 0 && !gpm_idle_claim(a.ring_seq, a.ring_ids, a.ring_cap, &ctl->q_head, &wid)) wid = -1;
+                    wid = __shfl_sync(GPM_FULL_MASK, wid, 0);
+                    if (wid < 0) break;
+                    unsigned char* box = a.mbox + (size_t)wid * a.mbox_stride;
+                    int32_t* dst = reinterpret_cast<int32_t*>(box + MT_PAYLOAD_OFF);
                     const int32_t* src = t == pdepth ? unit_ext : a.slab + a.lvl_off[t];
                     for (int z = start + lane; z < len; z += 32) dst[z - start] = src[z];
                     if (lane == 0) {
@@ -285,14 +307,14 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
                         u.child_hi = to - start;
                         for (int z = 0; z < MT_MAXK; z++) u.sub[z] = z < t ? W->sub[z] : -1;
                         u.list_off = -1;
-                        a.qunits[slot] = u;
+                        *reinterpret_cast<MotifUnit*>(box + sizeof(MailHdr)) = u;
                         W->hi[t] = start;
                         atomicAdd((unsigned long long*)&ctl->pending, 1ull);
                     }
                     __threadfence();
                     __syncwarp();
                     if (lane == 0) {
-                        gpm_q_publish(a.qseq, a.qcap, pos);
+                        atomicExch(&reinterpret_cast<MailHdr*>(box)->ready, 1);
                         atomicAdd(&ctl->donations, 1ull);
                     }
                     __syncwarp();

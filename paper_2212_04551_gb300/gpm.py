@@ -44,7 +44,7 @@ class gpm_config(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("donate_min", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
-                ("donate_after_us", ctypes.c_int32)]
+                ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32)]
 
 
 class gpm_stats(ctypes.Structure):
@@ -409,7 +409,7 @@ def gpm_batch_autotune(b: Batch, clique_k: int, motif_k: int, reps: int = 3):
 
 def gpm_batch_set_config(b: Batch, **kw) -> None:
     c = gpm_config()
-    c.warps_per_block = 8
+    c.warps_per_block = 0
     c.donate_min = 4
     c.order = GPM_ORDER_DEGREE_DESC
     c.max_idle_ms = 120000

@@ -23,6 +23,7 @@ default_rng(seed)`` (PCG64) so that any machine rebuilds identical bytes:
 """
 from __future__ import annotations
 
+import functools
 import hashlib
 from dataclasses import dataclass
 
@@ -295,7 +296,9 @@ def sample_roots(n: int, count: int, seed: int, exclude=None) -> np.ndarray:
     return np.sort(rng.choice(pool, size=count, replace=False)).astype(np.int32)
 
 
-# Workloads used by the tests and the benchmark, named by what they are.
+# Workloads used by the tests and the benchmark, named by what they are
+# (cached in-process: the graphs are immutable once built).
+@functools.lru_cache(maxsize=8)
 def workload(name: str):
     if name == "er516":
         return erdos_renyi_m(516, 1200, 0)
@@ -304,7 +307,7 @@ def workload(name: str):
     if name == "rmat16":
         return rmat(16, 8, 0.57, 0.19, 0.19, 2)
     if name == "ba4096":
-        return barabasi_albert_batch(4096, 20, 400, 2, 6, 3)
+        return tuple(barabasi_albert_batch(4096, 20, 400, 2, 6, 3))
     if name == "sbm2000":
         return sbm(2000, 100, 0.5, 0.01, 4)
     raise KeyError(name)
