@@ -162,6 +162,9 @@ typedef struct {
     int32_t donate;            /* 0 disables work donation                             */
     int32_t donate_after_us;   /* a unit is split only after it has run this long      */
     int32_t clique_tail;       /* clique levels finished lane-parallel: 2 or 3 (0: 3 for k >= 7, else 2) */
+    int32_t clique_compact;    /* two-level clique tail on the node's members (rows of ceil(|C|/32)   */
+                               /* words instead of ceil(d/32)): 0 never, 1 when |C| >= 48 and the    */
+                               /* rows get shorter, 2 whenever they get shorter                     */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */
@@ -179,8 +182,12 @@ typedef struct {
     uint64_t idle_polls;       /* times an idle warp polled the queue             */
     int32_t  grid_blocks;      /* persistent grid size                            */
     int32_t  warps_per_block;
-    uint64_t word_ops;         /* clique: 32-bit candidate-word AND+POPC operations */
+    uint64_t word_ops;         /* clique: 32-bit candidate-word AND+POPC operations; */
+                               /* motif: adjacency entries scanned                   */
     int32_t  kernel_launches;  /* kernels the call launched (enumeration path)    */
+    uint64_t busy_warp_ns;     /* sum over the grid's warps of the time spent      */
+                               /* inside work units (%globaltimer); 1 - busy /     */
+                               /* (warps x kernel time) is the idle warp fraction  */
 } gpm_stats;
 
 gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);

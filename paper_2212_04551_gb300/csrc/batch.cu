@@ -63,6 +63,7 @@ struct BatchParams {
     const int32_t* __restrict__ off;      // DAG
     const int32_t* __restrict__ adj;
     const int32_t* __restrict__ outdeg;
+    const int32_t* __restrict__ deg;
     const int32_t* __restrict__ goff;
     const int32_t* __restrict__ vgraph;
     const int32_t* __restrict__ units;    // (task << 31) | root
@@ -71,7 +72,7 @@ struct BatchParams {
     int npat;
     const uint16_t* __restrict__ lut;
     // shared-memory layout (bytes per warp)
-    int cq_maxd, cq_wmax, cq_ws, cq_words;
+    int cq_maxd, cq_wmax, cq_words;
     int mark_stride;
     long long lvl_off[MT_MAXK + 1];
     int slab_ints;
@@ -88,12 +89,13 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     unsigned char* base = smem_raw + (size_t)wib * p.warp_bytes;
     // clique part
     uint32_t* cq = reinterpret_cast<uint32_t*>(base);
-    const CqLayout L = cq_layout(p.cq_maxd, p.cq_wmax, p.cq_ws);
+    const CqLayout L = cq_layout(p.cq_maxd, p.cq_wmax, false);
     CliqueUnit* unit = reinterpret_cast<CliqueUnit*>(cq + L.unit);
     CliqueWalk cw;
     cw.off = p.off;
     cw.adj = p.adj;
     cw.outdeg = p.outdeg;
+    cw.deg = p.deg;
     cw.k_lo = p.kc;
     cw.k_hi = p.kc;
     cw.wmax = p.cq_wmax;
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     cw.donate_min = 0;
     cw.donate_after_ns = 0;
     cw.tail_levels = 0;
+    cw.compact = 0;
     // motif part
     unsigned char* mt = base + (size_t)p.cq_words * 4;
     MtWarp* W = reinterpret_cast<MtWarp*>(mt);
@@ -143,8 +146,10 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     WarpSink sink{wc};
     int cached_root = -1;
     Control* ctl = p.ctl;
+    unsigned long long busy = 0;      // time spent inside work units (%globaltimer ns)
 
     for (;;) {
+        const unsigned long long t_unit = gpm_globaltimer();
         unsigned long long u = 0;
         if (lane == 0) {
             u = *(volatile unsigned long long*)&ctl->next_root;
@@ -180,15 +185,15 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
             if (lane == 0) W->sub[0] = r;
             __syncwarp();
             mt_setup_prefix(mw, W, 1, lane);
-            const int lo = mt_root_ext_begin(p.indptr, p.indices, r);
+            const int lo = mt_root_ext_begin(p.indptr, p.indices, r, lane);
             if (lane == 0) {
                 W->len[1] = p.indptr[r + 1] - lo;
                 W->cur[1] = 0;
                 W->hi[1] = p.indptr[r + 1] - lo;
             }
             __syncwarp();
-            unsigned long long leaves = 0;
-            mt_walk<false>(mw, W, 1, r, 0, p.indices + lo, sink, leaves, lane);
+            unsigned long long leaves = 0, scanned = 0;
+            mt_walk<false>(mw, W, 1, r, 0, p.indices + lo, sink, leaves, scanned, lane);
             mt_clear_prefix(mw, W, 1, lane);
             __syncwarp();
             for (int j = lane; j < p.npat; j += 32) {
@@ -202,7 +207,9 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
             __syncwarp();
         }
         if (lane == 0) atomicAdd(&ctl->units_done, 1ull);
+        busy += gpm_globaltimer() - t_unit;
     }
+    if (lane == 0) atomicAdd(&ctl->busy_ns, busy);
 }
 
 // units: (task << 31) | root.  Mode 0: every motif root (heaviest degree
@@ -261,6 +268,7 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     p.off = kc > 0 ? g->dag_off.as<int32_t>() : nullptr;
     p.adj = kc > 0 ? g->dag_adj.as<int32_t>() : nullptr;
     p.outdeg = kc > 0 ? g->dag_outdeg.as<int32_t>() : nullptr;
+    p.deg = kc > 0 ? g->degree.as<int32_t>() : nullptr;
     p.goff = b->goff.as<int32_t>();
     p.vgraph = b->vgraph.as<int32_t>();
     p.units = units.as<int32_t>();
@@ -272,8 +280,7 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     if (kc > 0 && g->max_outdeg > 1024) fail(GPM_ENOTIMPL, "batched clique counting needs out-degrees <= 1024");
     p.cq_maxd = std::max(kc > 0 ? g->max_outdeg : 1, 1);
     p.cq_wmax = (p.cq_maxd + 31) / 32;
-    p.cq_ws = p.cq_wmax | 1;
-    p.cq_words = cq_layout(p.cq_maxd, p.cq_wmax, p.cq_ws).total;
+    p.cq_words = cq_layout(p.cq_maxd, p.cq_wmax, false).total;
     p.mark_stride = (b->max_graph_n + 15) & ~15;
     long long off = 0;
     const long long D = std::max(g->max_deg, 1);
@@ -459,11 +466,13 @@ void batch_count(gpm_batch* b, int kc, int km, uint64_t* clique_counts, uint64_t
     gpm_stats st{};
     st.kernel_ms = ms;
     st.units_done = h->units_done;
+    st.busy_warp_ns = h->busy_ns;
     st.kernel_launches = 1;
     st.grid_blocks = cap.blocks;
     st.warps_per_block = cap.wpb;
     b->stats = st;
     if (h->error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
+    if (h->error >= DEV_ECHECK) fail(GPM_ECUDA, "device consistency check " + std::to_string(h->error - DEV_ECHECK) + " failed");
     if (h->error) fail(GPM_ECUDA, "device error " + std::to_string(h->error));
     if (h->overflow) fail(GPM_EOVERFLOW, "a per-graph count exceeds 2^64-1");
     if (kc > 0) std::copy(cap.host_out, cap.host_out + G, clique_counts);

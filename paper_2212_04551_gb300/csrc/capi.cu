@@ -224,6 +224,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.max_idle_ms <= 0) fail(GPM_EINVAL, "max_idle_ms must be positive");
         if (c.donate_after_us < 0) fail(GPM_EINVAL, "donate_after_us < 0");
         if (c.clique_tail != 0 && c.clique_tail != 2 && c.clique_tail != 3) fail(GPM_EINVAL, "clique_tail must be 0, 2 or 3");
+        if (c.clique_compact < 0 || c.clique_compact > 2) fail(GPM_EINVAL, "clique_compact must be 0, 1 or 2");
         g->cfg = c;
     });
 }

@@ -46,11 +46,11 @@ struct CliqueParams {
     const int32_t* __restrict__ off;
     const int32_t* __restrict__ adj;
     const int32_t* __restrict__ outdeg;
+    const int32_t* __restrict__ deg;
     const int32_t* __restrict__ roots;
     long long n_roots;
     int k_lo, k_hi;
     int wmax;            // 32-bit words per bitmap row at the largest out-degree
-    int ws;              // row stride in words (odd: lanes reading different rows hit different banks)
     int maxd;
     int stride_words;    // shared-memory words per warp
     Control* ctl;
@@ -66,13 +66,14 @@ struct CliqueParams {
     unsigned long long donate_after_ns;
     unsigned long long max_idle_ns;
     int tail_levels;
+    int compact;
 };
 
-__global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
+__global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const CqLayout L = cq_layout(p.maxd, p.wmax, p.ws);
+    const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0);
     uint32_t* base = smem + (size_t)wib * p.stride_words;
     unsigned long long* wcnt = reinterpret_cast<unsigned long long*>(base + L.wcnt);
     CliqueUnit* unit = reinterpret_cast<CliqueUnit*>(base + L.unit);
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     walk.off = p.off;
     walk.adj = p.adj;
     walk.outdeg = p.outdeg;
+    walk.deg = p.deg;
     walk.k_lo = p.k_lo;
     walk.k_hi = p.k_hi;
     walk.wmax = p.wmax;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     walk.donate_min = p.donate_min;
     walk.donate_after_ns = p.donate_after_ns;
     walk.tail_levels = p.tail_levels;
+    walk.compact = p.compact;
 
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
     unsigned long long top_km1 = 0;   // lane-private (k_hi-1)-clique count
@@ -118,6 +121,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     int spin = 0;
     long long last_pending = -1;
     unsigned long long idle_since = 0;
+    unsigned long long busy = 0;      // time spent inside work units (%globaltimer ns)
     bool aborted = false;
 
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // this warp's global id
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
         }
         idle = false;
         spin = 0;
+        const unsigned long long t_unit = gpm_globaltimer();
 
         // ---- process the unit
         const int root_pos = unit->root_pos;
@@ -210,6 +215,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
             atomicAdd(&ctl->units_done, 1ull);
             atomicAdd((unsigned long long*)&ctl->pending, (unsigned long long)-1ll);
         }
+        busy += gpm_globaltimer() - t_unit;
     }
 
     const unsigned long long tot = gpm_warp_sum(top_sum);
@@ -219,6 +225,7 @@ __global__ void __launch_bounds__(512) k_clique(CliqueParams p) {
     if (lane == 0) {
         atomicAdd(&ctl->word_ops, wsum);
         if (polls) atomicAdd(&ctl->idle_polls, polls);
+        atomicAdd(&ctl->busy_ns, busy);
         add_count(ctl, p.k_hi, tot);
         if (p.k_hi >= 4 && p.k_hi - 1 >= p.k_lo) add_count(ctl, p.k_hi - 1, km1);
         for (int j = p.k_lo; j < p.k_hi - 1; j++) add_count(ctl, j, wcnt[j]);
@@ -301,14 +308,15 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         p.off = g->dag_off.as<int32_t>();
         p.adj = g->dag_adj.as<int32_t>();
         p.outdeg = g->dag_outdeg.as<int32_t>();
+        p.deg = g->degree.as<int32_t>();
         p.roots = d_roots;
         p.n_roots = n_counter;
         p.k_lo = std::max(k_lo, 3);
         p.k_hi = k_hi;
         p.maxd = std::max(g->max_outdeg, 1);
         p.wmax = (p.maxd + 31) / 32;
-        p.ws = p.wmax | 1;
-        const CqLayout L = cq_layout(p.maxd, p.wmax, p.ws);
+        p.compact = g->cfg.clique_compact;   // before the layout: it sizes the compaction region
+        const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0);
         p.stride_words = L.total;
         int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block
                                               : best_warps_per_block((const void*)k_clique, (size_t)L.total * 4, 0);
@@ -367,6 +375,7 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
     st.donations = h.donations;
     st.idle_polls = h.idle_polls;
     st.word_ops = h.word_ops;
+    st.busy_warp_ns = h.busy_ns;
     st.kernel_launches = st.grid_blocks ? (n_split > 0 ? 3 : 2) : (k_hi <= 2 && n_roots > 0 ? 1 : 0);
     g->stats = st;
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");

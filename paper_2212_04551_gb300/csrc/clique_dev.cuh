@@ -32,6 +32,8 @@ constexpr int CQ_LEVELS = GPM_CLIQUE_MAX_K + 1;
 constexpr int CQ_MAX_OUTDEG = 1024;          // bitmap rows of at most 32 words
 
 constexpr int CQ_PAIR_FLUSH = 128;            // run the pair batch once it holds this many
+constexpr int CQ_CW = 5;                      // compacted tail: at most 32 * CQ_CW members
+constexpr int CQ_COMPACT_MIN = 48;            // ... and (clique_compact = 1) at least this many
 
 struct CliqueUnit {
     int32_t root_pos;                   // index into the root list
@@ -43,12 +45,42 @@ static_assert(sizeof(CliqueUnit) % 4 == 0, "unit must be word-sized");
 
 
 
+// words of the pair / compacted-matrix region: the pair batch, or (with the
+// compacted tail on and rows of at least three words) up to 32 * CQ_CW
+// members x CQ_CW words
+__host__ __device__ inline int cq_pairs_words(int wmax, bool compact) {
+    const int pairs = CQ_PAIR_FLUSH + 32 * wmax;
+    const int cm = (compact && wmax >= 3) ? min(32 * wmax, 32 * CQ_CW) * CQ_CW : 0;
+    return pairs > cm ? pairs : cm;
+}
+
+// Root-local bit rows, stored upper-triangular: row p (positions in
+// orientation order) can only hold positions above p, so its words below
+// p / 32 are zero and are not stored.  Rows of block b (positions 32b ..
+// 32b + 31) keep w - b words; row(p)[z] is word z of row p for z >= p / 32.
+__host__ __device__ inline int cq_tri_words(int d, int w) {
+    const int b = d >> 5;
+    return 32 * (b * w - b * (b - 1) / 2) + (d - 32 * b) * (w - b);
+}
+
+struct TriRows {                    // the root-local matrix
+    const uint32_t* base;
+    int w;
+    __device__ __forceinline__ const uint32_t* row(int p) const { return base + cq_tri_words(p, w) - (p >> 5); }
+};
+
+struct RectRows {                   // a plain row-major matrix (the compacted one)
+    const uint32_t* base;
+    int ws;
+    __device__ __forceinline__ const uint32_t* row(int p) const { return base + p * ws; }
+};
+
 // shared-memory layout of one warp, in 32-bit words
 struct CqLayout {
     int wcnt, unit, cur, hi, cand, list, pairs, rows, total;
 };
 
-__host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, int ws) {
+__host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, bool compact) {
     CqLayout L;
     L.wcnt = 0;                                        // CQ_LEVELS x u64
     L.unit = L.wcnt + 2 * CQ_LEVELS;                   // CliqueUnit
@@ -56,9 +88,10 @@ __host__ __device__ inline CqLayout cq_layout(int maxd, int wmax, int ws) {
     L.hi = L.cur + CQ_LEVELS;
     L.cand = L.hi + CQ_LEVELS;                         // CQ_LEVELS x wmax candidate bitmaps
     L.list = L.cand + CQ_LEVELS * wmax;                // 32*wmax ints: N+(r), later the child list
-    L.pairs = L.list + 32 * wmax;                      // pair batch of the three-level tail
-    L.rows = L.pairs + CQ_PAIR_FLUSH + 32 * wmax;      // maxd x ws bit rows
-    L.total = L.rows + maxd * ws;
+    L.pairs = L.list + 32 * wmax;                      // pair batch of the three-level tail,
+                                                       // or the compacted matrix of the two-level one
+    L.rows = L.pairs + cq_pairs_words(wmax, compact);  // upper-triangular bit rows
+    L.total = L.rows + cq_tri_words(maxd, wmax);
     L.total = (L.total + 3) & ~3;                      // keep every warp 16-byte aligned
     return L;
 }
@@ -94,18 +127,42 @@ __device__ __forceinline__ void add_count(Control* ctl, int j, unsigned long lon
     if (old + v < old) atomicExch(&ctl->overflow, 1);
 }
 
-// Build the root-local bit matrix: row i = N+(u_i) restricted to N+(r).
+// Build the root-local bit matrix.  The out-neighbours u of r get local
+// positions in orientation order -- ascending (degree, id), the order that
+// defines the DAG -- so that row p (the out-neighbours of the vertex at
+// position p, restricted to N+(r)) holds only positions above p: every
+// candidate set below position p lies in the words from p / 32 on.
+// list[] receives N+(r) in id order (for the binary searches), pos[] each
+// entry's position; both are scratch for the caller after the build.
 __device__ __noinline__ static void build_rows(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
-                           const int32_t* __restrict__ outdeg, int r, int d, int ws, int* list, uint32_t* rows,
-                           int lane) {
+                                               const int32_t* __restrict__ outdeg, const int32_t* __restrict__ deg,
+                                               int r, int d, int* list, int* pos, uint32_t* rows, int lane) {
     const int beg = off[r];
-    for (int t = lane; t < d; t += 32) list[t] = adj[beg + t];
-    for (int t = lane; t < d * ws; t += 32) rows[t] = 0u;
+    for (int t = lane; t < d; t += 32) {
+        const int u = adj[beg + t];
+        list[t] = u;
+        rows[t] = deg[u];               // sort keys, staged in the (not yet cleared) rows
+    }
+    __syncwarp();
+    for (int t = lane; t < d; t += 32) {
+        const int kt = rows[t];
+        int p = 0;
+        for (int s = 0; s < d; s++) {   // rank by (degree, id); ids ascend with s
+            const int ks = rows[s];
+            p += (ks < kt || (ks == kt && s < t)) ? 1 : 0;
+        }
+        pos[t] = p;
+    }
+    __syncwarp();
+    const int w = (d + 31) >> 5;
+    const int total = cq_tri_words(d, w);
+    for (int t = lane; t < total; t += 32) rows[t] = 0u;
     __syncwarp();
     const int first = list[0], last = list[d - 1];
     for (int i = 0; i < d; i++) {
         const int u = list[i];
         const int ub = off[u], du = outdeg[u];
+        uint32_t* row = rows + cq_tri_words(pos[i], w) - (pos[i] >> 5);   // words >= pos[i] / 32
         for (int t = lane; t < du; t += 32) {
             const int x = adj[ub + t];
             if (x < first || x > last) continue;
@@ -114,7 +171,10 @@ __device__ __noinline__ static void build_rows(const int32_t* __restrict__ off, 
                 const int mid = (lo + hi) >> 1;
                 if (list[mid] < x) lo = mid + 1; else hi = mid;
             }
-            if (list[lo] == x) atomicOr(&rows[i * ws + (lo >> 5)], 1u << (lo & 31));
+            const int px = list[lo] == x ? pos[lo] : -1;
+            if (px > pos[i]) {              // always, in the orientation; guards the triangle
+                atomicOr(&row[px >> 5], 1u << (px & 31));
+            }
         }
     }
     __syncwarp();
@@ -126,6 +186,7 @@ struct CliqueWalk {
     const int32_t* __restrict__ off;
     const int32_t* __restrict__ adj;
     const int32_t* __restrict__ outdeg;
+    const int32_t* __restrict__ deg;    // undirected degrees (the orientation's key)
     int k_lo, k_hi;
     int wmax;
     // this warp's shared memory
@@ -146,6 +207,8 @@ struct CliqueWalk {
     int donate_min;
     unsigned long long donate_after_ns;   // a unit splits only after running this long
     int tail_levels;                      // 2 or 3 (0: 3)
+    int compact;                          // compacted two-level tail: 0 never, 1 large nodes, 2 whenever shorter
+    __device__ uint32_t* pairs_u32() const { return reinterpret_cast<uint32_t*>(pairs); }
 };
 
 // Compact the children of a node (set bits of C in [from, to)) into list[];
@@ -165,10 +228,11 @@ __device__ __forceinline__ int cq_compact(const uint32_t* C, int w, int from, in
 
 // sum over the set bits l of x (W >= w words, in registers) of
 // popc(x & row_l): the cliques one level below the node whose candidates are
-// x.  Two rows are loaded per step so that each lane has two independent
+// x.  Row l is zero below word l / 32, so only words from there on are read.
+// Two rows are loaded per step so that each lane has two independent
 // shared-memory loads in flight.
-template <int W>
-__device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const uint32_t* rows, int w, int ws) {
+template <int W, class Rows>
+__device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const Rows& rows, int w) {
     unsigned acc = 0;
     for (int q = 0; q < w; q++) {
         // word q of x without dynamic register indexing
@@ -179,23 +243,23 @@ __device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const ui
         while (bits) {
             const int l1 = 32 * q + __ffs(bits) - 1;
             bits &= bits - 1u;
-            const uint32_t* r1 = rows + l1 * ws;
+            const uint32_t* r1 = rows.row(l1);
             if (bits) {
                 const int l2 = 32 * q + __ffs(bits) - 1;
                 bits &= bits - 1u;
-                const uint32_t* r2 = rows + l2 * ws;
+                const uint32_t* r2 = rows.row(l2);
                 uint32_t a[W], b[W];
 #pragma unroll
                 for (int z = 0; z < W; z++) {
-                    a[z] = z < w ? r1[z] : 0u;
-                    b[z] = z < w ? r2[z] : 0u;
+                    a[z] = (z >= q && z < w) ? r1[z] : 0u;
+                    b[z] = (z >= q && z < w) ? r2[z] : 0u;
                 }
 #pragma unroll
                 for (int z = 0; z < W; z++) acc += __popc(x[z] & a[z]) + __popc(x[z] & b[z]);
             } else {
 #pragma unroll
                 for (int z = 0; z < W; z++)
-                    if (z < w) acc += __popc(x[z] & r1[z]);
+                    if (z >= q && z < w) acc += __popc(x[z] & r1[z]);
             }
         }
     }
@@ -208,57 +272,135 @@ __device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const ui
 // km1) and, for every j in C_i, adds popc(C_i & row_j) -- the k-cliques
 // through (i, j), aggregate_counter on each (k-1)-clique.  W >= w words.
 template <int W>
-__device__ __forceinline__ void cq_tail2(const uint32_t* C, const uint32_t* rows, int w, int ws, const int* list,
+__device__ __forceinline__ void cq_tail2(const uint32_t* C, const TriRows& rows, int w, const int* list,
                                          int nchild, unsigned long long& km1, unsigned long long& kk,
                                          unsigned long long& wops, int lane) {
     uint32_t c[W];
 #pragma unroll
     for (int q = 0; q < W; q++) c[q] = q < w ? C[q] : 0u;
     for (int t = lane; t < nchild; t += 32) {
-        const uint32_t* ri = rows + list[t] * ws;
+        const int pi = list[t];
+        const int bi = pi >> 5;
+        const uint32_t* ri = rows.row(pi);
         uint32_t ci[W];
         int g = 0;
 #pragma unroll
         for (int q = 0; q < W; q++) {
-            ci[q] = q < w ? (c[q] & ri[q]) : 0u;
+            ci[q] = (q >= bi && q < w) ? (c[q] & ri[q]) : 0u;
             g += __popc(ci[q]);
         }
         km1 += (unsigned)g;
         wops += (unsigned long long)(g + 1) * (unsigned)w;
-        kk += cq_sum_rows<W>(ci, rows, w, ws);
+        kk += cq_sum_rows<W>(ci, rows, w);
     }
 }
 
-__device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint32_t* rows, int w, int ws,
-                                                  const int* list, int nchild, unsigned long long& km1,
-                                                  unsigned long long& kk, unsigned long long& wops, int lane) {
-    if (w <= 1) cq_tail2<1>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
-    else if (w <= 2) cq_tail2<2>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
-    else if (w <= 4) cq_tail2<4>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
-    else if (w <= 6) cq_tail2<6>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
-    else if (w <= 8) cq_tail2<8>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
-    else if (w <= 10) cq_tail2<10>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
-    else if (w <= 16) cq_tail2<16>(C, rows, w, ws, list, nchild, km1, kk, wops, lane);
+__device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const TriRows& rows, int w, const int* list,
+                                                  int nchild, unsigned long long& km1, unsigned long long& kk,
+                                                  unsigned long long& wops, int lane) {
+    if (w <= 1) cq_tail2<1>(C, rows, w, list, nchild, km1, kk, wops, lane);
+    else if (w <= 2) cq_tail2<2>(C, rows, w, list, nchild, km1, kk, wops, lane);
+    else if (w <= 4) cq_tail2<4>(C, rows, w, list, nchild, km1, kk, wops, lane);
+    else if (w <= 6) cq_tail2<6>(C, rows, w, list, nchild, km1, kk, wops, lane);
+    else if (w <= 8) cq_tail2<8>(C, rows, w, list, nchild, km1, kk, wops, lane);
+    else if (w <= 10) cq_tail2<10>(C, rows, w, list, nchild, km1, kk, wops, lane);
     else {
-        // wide rows (out-degree > 512): C_i's words are recomputed from shared
+        // wide rows (out-degree > 320): C_i's words are recomputed from shared
         // memory instead of held in registers
         for (int t = lane; t < nchild; t += 32) {
-            const uint32_t* ri = rows + list[t] * ws;
+            const int pi = list[t];
+            const uint32_t* ri = rows.row(pi);
             unsigned long long acc = 0;
-            for (int q = 0; q < w; q++) {
+            for (int q = pi >> 5; q < w; q++) {
                 uint32_t bits = C[q] & ri[q];
                 km1 += (unsigned)__popc(bits);
                 wops += (unsigned long long)(__popc(bits) + 1) * (unsigned)w;
                 while (bits) {
                     const int j = 32 * q + __ffs(bits) - 1;
                     bits &= bits - 1u;
-                    const uint32_t* rj = rows + j * ws;
-                    for (int z = 0; z < w; z++) acc += __popc(C[z] & ri[z] & rj[z]);
+                    const uint32_t* rj = rows.row(j);
+                    for (int z = q; z < w; z++) acc += __popc(C[z] & ri[z] & rj[z]);
                 }
             }
             kk += acc;
         }
     }
+}
+
+// The last two levels below a node of size k-3, on the node's own members:
+// member m is the m-th set bit of C (ascending position), and R[m] -- row m
+// of a c x c bit matrix, c = |C| -- holds the members adjacent to it from
+// its out-neighbourhood (only members above m, the positions being in
+// orientation order).  The counts are those of cq_tail2 on the same
+// children, but every row operation touches ceil(c/32) words instead of
+// ceil(d/32).  The matrix is built by ballots: lane t holds the position of
+// member 32b + t, and bit t of R[m]'s word b is that position's bit in the
+// root-local row of member m.  Children: the members with positions in
+// [from, to).  mem: c ints of scratch; R: c x (W2 | 1) words.
+template <int W2>
+__device__ __forceinline__ void cq_tail2c(const uint32_t* C, const TriRows& rows, int w, int c, int from,
+                                          int to, int* mem, uint32_t* R, unsigned long long& nchild,
+                                          unsigned long long& km1, unsigned long long& kk,
+                                          unsigned long long& wops, int lane) {
+    int n = 0, m_lo = 0, m_hi = 0;
+    for (int q = 0; q < w; q++) {
+        const uint32_t word = C[q];
+        const bool bit = (word >> lane) & 1u;
+        const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
+        if (bit) mem[n + __popc(bal & gpm_lanemask_lt())] = 32 * q + lane;
+        n += __popc(bal);
+        m_lo += __popc(bal & range_mask(q, 0, from));
+        m_hi += __popc(bal & range_mask(q, 0, to));
+    }
+    __syncwarp();
+    const int w2 = (c + 31) >> 5;
+    const int ws2 = w2 | 1;
+    int pm[W2];
+#pragma unroll
+    for (int b = 0; b < W2; b++) pm[b] = (b < w2 && 32 * b + lane < c) ? mem[32 * b + lane] : -1;
+    for (int m = 0; m < c; m++) {
+        const int pmm = mem[m];
+        const uint32_t* row = rows.row(pmm);
+        uint32_t* Rm = R + m * ws2;
+#pragma unroll
+        for (int b = 0; b < W2; b++) {
+            if (b < w2) {
+                uint32_t word = 0u;
+                if (b >= (m >> 5)) {      // members above m only: earlier words are empty
+                    const bool bit = pm[b] > pmm && ((row[pm[b] >> 5] >> (pm[b] & 31)) & 1u);
+                    word = __ballot_sync(GPM_FULL_MASK, bit);
+                }
+                if (lane == b) Rm[b] = word;
+            }
+        }
+    }
+    __syncwarp();
+    for (int m = m_lo + lane; m < m_hi; m += 32) {
+        const uint32_t* Rm = R + m * ws2;
+        uint32_t x[W2];
+        int g = 0;
+#pragma unroll
+        for (int z = 0; z < W2; z++) {
+            x[z] = z < w2 ? Rm[z] : 0u;
+            g += __popc(x[z]);
+        }
+        km1 += (unsigned)g;
+        wops += (unsigned long long)g * (unsigned)w2;
+        kk += cq_sum_rows<W2>(x, RectRows{R, ws2}, w2);
+    }
+    nchild = (unsigned long long)(m_hi - m_lo);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void cq_tail2c_dispatch(const uint32_t* C, const TriRows& rows, int w, int c,
+                                                   int from, int to, int* mem, uint32_t* R,
+                                                   unsigned long long& nchild, unsigned long long& km1,
+                                                   unsigned long long& kk, unsigned long long& wops, int lane) {
+    const int w2 = (c + 31) >> 5;
+    if (w2 <= 2) cq_tail2c<2>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
+    else if (w2 <= 3) cq_tail2c<3>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
+    else if (w2 <= 4) cq_tail2c<4>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
+    else cq_tail2c<5>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
 }
 
 // Pairs (i, j) -- a child i of a node of size k-4 and a child j of i -- in
@@ -267,23 +409,25 @@ __device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const uint3
 // (k-1)-cliques through (i, j)), then popc(C_ij & row_l) for every l in C_ij
 // adds the k-cliques: aggregate_counter on every (k-1)-clique.
 template <int W>
-__device__ __forceinline__ void cq_pairs_run(const uint32_t (&c)[W], const uint32_t* rows, int w, int ws,
+__device__ __forceinline__ void cq_pairs_run(const uint32_t (&c)[W], const TriRows& rows, int w,
                                              const int* pairs, int np, unsigned long long& km1,
                                              unsigned long long& kk, unsigned long long& wops, int lane) {
     for (int t = lane; t < np; t += 32) {
         const int pr = pairs[t];
-        const uint32_t* ri = rows + (pr >> 16) * ws;
-        const uint32_t* rj = rows + (pr & 0xffff) * ws;
+        const int pj = pr & 0xffff;          // j > i: both rows are stored from word pj / 32 on
+        const int bj = pj >> 5;
+        const uint32_t* ri = rows.row(pr >> 16);
+        const uint32_t* rj = rows.row(pj);
         uint32_t cij[W];
         int g = 0;
 #pragma unroll
         for (int z = 0; z < W; z++) {
-            cij[z] = z < w ? (c[z] & ri[z] & rj[z]) : 0u;
+            cij[z] = (z >= bj && z < w) ? (c[z] & ri[z] & rj[z]) : 0u;
             g += __popc(cij[z]);
         }
         km1 += (unsigned)g;
         wops += (unsigned long long)(g + 1) * (unsigned)w;
-        kk += cq_sum_rows<W>(cij, rows, w, ws);
+        kk += cq_sum_rows<W>(cij, rows, w);
     }
 }
 
@@ -295,7 +439,7 @@ __device__ __forceinline__ void cq_pairs_run(const uint32_t (&c)[W], const uint3
 // pair, however few children each node has.  Uniform counts: n3 children
 // (size k-3), n2 pairs (size k-2).
 template <int W>
-__device__ __forceinline__ void cq_tail3(const uint32_t* C, const uint32_t* rows, int w, int ws, int from, int to,
+__device__ __forceinline__ void cq_tail3(const uint32_t* C, const TriRows& rows, int w, int from, int to,
                                          int* pairs, unsigned long long& n3, unsigned long long& n2,
                                          unsigned long long& km1, unsigned long long& kk, unsigned long long& wops,
                                          int lane) {
@@ -309,8 +453,8 @@ __device__ __forceinline__ void cq_tail3(const uint32_t* C, const uint32_t* rows
             const int i = 32 * q + __ffs(word) - 1;
             word &= word - 1u;
             n3 += 1;
-            const uint32_t* ri = rows + i * ws;
-            for (int q2 = 0; q2 < w; q2++) {
+            const uint32_t* ri = rows.row(i);
+            for (int q2 = i >> 5; q2 < w; q2++) {
                 const uint32_t ciw = C[q2] & ri[q2];
                 const bool bit = (ciw >> lane) & 1u;
                 const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
@@ -321,7 +465,7 @@ __device__ __forceinline__ void cq_tail3(const uint32_t* C, const uint32_t* rows
             if (np >= CQ_PAIR_FLUSH) {
                 __syncwarp();
                 n2 += (unsigned)np;
-                cq_pairs_run<W>(c, rows, w, ws, pairs, np, km1, kk, wops, lane);
+                cq_pairs_run<W>(c, rows, w, pairs, np, km1, kk, wops, lane);
                 __syncwarp();
                 np = 0;
             }
@@ -330,22 +474,21 @@ __device__ __forceinline__ void cq_tail3(const uint32_t* C, const uint32_t* rows
     if (np) {
         __syncwarp();
         n2 += (unsigned)np;
-        cq_pairs_run<W>(c, rows, w, ws, pairs, np, km1, kk, wops, lane);
+        cq_pairs_run<W>(c, rows, w, pairs, np, km1, kk, wops, lane);
         __syncwarp();
     }
 }
 
-__device__ __forceinline__ void cq_tail3_dispatch(const uint32_t* C, const uint32_t* rows, int w, int ws, int from,
-                                                  int to, int* pairs, unsigned long long& n3, unsigned long long& n2,
+__device__ __forceinline__ void cq_tail3_dispatch(const uint32_t* C, const TriRows& rows, int w, int from, int to,
+                                                  int* pairs, unsigned long long& n3, unsigned long long& n2,
                                                   unsigned long long& km1, unsigned long long& kk,
                                                   unsigned long long& wops, int lane) {
-    if (w <= 1) cq_tail3<1>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 2) cq_tail3<2>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 4) cq_tail3<4>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 6) cq_tail3<6>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 8) cq_tail3<8>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 10) cq_tail3<10>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else cq_tail3<16>(C, rows, w, ws, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    if (w <= 1) cq_tail3<1>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 2) cq_tail3<2>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 4) cq_tail3<4>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 6) cq_tail3<6>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else if (w <= 8) cq_tail3<8>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
+    else cq_tail3<10>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
 }
 
 // Walk one unit (root r = roots[root_pos], d = |N+(r)|).  Returns false if it
@@ -356,18 +499,17 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                         unsigned long long& unit_sum, unsigned long long& km1, unsigned long long& wops, int lane) {
     if (d < a.k_lo - 1 || d <= 0) return true;
     const int w = (d + 31) >> 5;
-    const int ws = w | 1;
     const int K = a.k_hi;
     unsigned long long* wcnt = a.wcnt;
     int* cur = a.cur;
     int* hiv = a.hiv;
     uint32_t* cand = a.cand;
     int* list = a.list;
-    uint32_t* rows = a.rows;
     if (r != cached_root) {
-        build_rows(a.off, a.adj, a.outdeg, r, d, ws, list, rows, lane);
+        build_rows(a.off, a.adj, a.outdeg, a.deg, r, d, list, a.pairs, a.rows, lane);
         cached_root = r;
     }
+    const TriRows rows{a.rows, w};
     // candidates of the unit's node: all of N+(r), then AND along the path
     if (lane < w) cand[1 * a.wmax + lane] = range_mask(lane, 0, d);
     __syncwarp();
@@ -375,7 +517,8 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
     int s = 1;
     for (int t = 0; t < depth; t++) {
         const int i = unit->path[t];
-        if (lane < w) cand[(s + 1) * a.wmax + lane] = cand[s * a.wmax + lane] & rows[i * ws + lane];
+        if (lane < w)
+            cand[(s + 1) * a.wmax + lane] = lane >= (i >> 5) ? (cand[s * a.wmax + lane] & rows.row(i)[lane]) : 0u;
         s++;
         __syncwarp();
     }
@@ -388,7 +531,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
     // nodes of size `tail` are finished by the lane-parallel tail: three
     // levels (by default for k >= 7, where the pair batches keep every lane
     // busy; measured slower than two levels at k = 6), else two, else one
-    const bool three = w <= 16 && K >= 5 && (a.tail_levels == 3 || (a.tail_levels == 0 && K >= 7));
+    const bool three = w <= 10 && K >= 5 && (a.tail_levels == 3 || (a.tail_levels == 0 && K >= 7));
     const int tail = three ? K - 4 : (K >= 4 ? K - 3 : 1);
     const unsigned long long t_start = DONATE ? gpm_globaltimer() : 0ull;
 
@@ -397,7 +540,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         const uint32_t* Cs = cand + s * a.wmax;
         if (s == tail && three) {
             unsigned long long n3 = 0, n2 = 0;
-            cq_tail3_dispatch(Cs, rows, w, ws, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
+            cq_tail3_dispatch(Cs, rows, w, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
             if (lane == 0) {
                 if (K - 3 >= a.k_lo) wcnt[K - 3] += n3;
                 if (K - 2 >= a.k_lo) wcnt[K - 2] += n2;
@@ -407,22 +550,38 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
             s--;
             continue;
         }
+        if (s == tail && K >= 4 && w >= 3 && a.compact != 0) {
+            // compact the node to its members when that shortens the rows
+            const int c = count_range(Cs, w, 0, d, lane);
+            const int w2 = (c + 31) >> 5;
+            if (w2 <= CQ_CW && w2 < w && (a.compact == 2 || c >= CQ_COMPACT_MIN)) {
+                unsigned long long nch = 0;
+                cq_tail2c_dispatch(Cs, rows, w, c, cur[s], hiv[s], list, a.pairs_u32(), nch, km1, unit_sum,
+                                   wops, lane);
+                if (lane == 0 && K - 2 >= a.k_lo) wcnt[K - 2] += nch;
+                __syncwarp();
+                if (s == s_base) break;
+                s--;
+                continue;
+            }
+        }
         if (s == tail) {
             const int nchild = cq_compact(Cs, w, cur[s], hiv[s], list, lane);
             if (K == 3) {
                 // one level: 3-cliques = sum over children of popc(C & row_i)
                 unsigned long long sum = 0;
                 for (int t = lane; t < nchild; t += 32) {
-                    const uint32_t* row = rows + list[t] * ws;
+                    const int pi = list[t];
+                    const uint32_t* row = rows.row(pi);
                     int c = 0;
-                    for (int q = 0; q < w; q++) c += __popc(Cs[q] & row[q]);
+                    for (int q = pi >> 5; q < w; q++) c += __popc(Cs[q] & row[q]);
                     sum += (unsigned)c;
                     wops += (unsigned)w;
                 }
                 unit_sum += sum;
             } else {
                 if (lane == 0 && K - 2 >= a.k_lo) wcnt[K - 2] += (unsigned)nchild;
-                cq_tail2_dispatch(Cs, rows, w, ws, list, nchild, km1, unit_sum, wops, lane);
+                cq_tail2_dispatch(Cs, rows, w, list, nchild, km1, unit_sum, wops, lane);
             }
             __syncwarp();
             if (s == s_base) break;
@@ -438,7 +597,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         uint32_t* Cn = cand + (s + 1) * a.wmax;
         uint32_t x = 0;
         if (lane < w) {
-            x = Cs[lane] & rows[i * ws + lane];
+            x = lane >= (i >> 5) ? (Cs[lane] & rows.row(i)[lane]) : 0u;
             Cn[lane] = x;
         }
         const int c = __reduce_add_sync(GPM_FULL_MASK, (unsigned)__popc(x));

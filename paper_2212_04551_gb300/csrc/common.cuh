@@ -135,13 +135,15 @@ struct Control {
     unsigned long long donations, units_done, idle_polls;
     unsigned long long word_ops;      // clique: 32-bit candidate-word AND+POPC operations
     unsigned long long next_seed;     // next pre-split seed unit
+    unsigned long long busy_ns;       // sum over warps of time spent inside work units
     int overflow;
     int pad;
 };
 
 // Device-side status values (mirrors gpm_status).
 enum : int { DEV_OK = 0, DEV_ETIMEOUT = GPM_ETIMEOUT, DEV_EOVERFLOW = GPM_EOVERFLOW,
-             DEV_EINVAL = GPM_EINVAL };
+             DEV_EINVAL = GPM_EINVAL,
+             DEV_ECHECK = 64 };   // + n: internal consistency check n failed (the access was skipped)
 
 // Launch geometry for a persistent kernel.
 struct Grid {

@@ -380,6 +380,7 @@ gpm_config default_config() {
     c.donate = 1;
     c.donate_after_us = 50;
     c.clique_tail = 0;
+    c.clique_compact = 0;
     return c;
 }
 

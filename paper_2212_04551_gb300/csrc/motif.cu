@@ -52,7 +52,7 @@ struct MotifParams {
 };
 
 template <bool SMEM_STATE>
-__global__ void __launch_bounds__(512) k_motif(MotifParams p) {
+__global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
 
     bool idle = false;
     unsigned long long polls = 0;
+    unsigned long long scanned = 0;   // adjacency entries scanned by this warp (lane 0)
     int spin = 0;
     long long last_pending = -1;
     unsigned long long idle_since = 0;
+    unsigned long long busy = 0;      // time spent inside work units (%globaltimer ns)
     bool aborted = false;
 
     unsigned char* my_box = p.mbox ? p.mbox + (size_t)gw * p.mbox_stride : nullptr;
@@ -119,11 +121,14 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
                 if (r < (unsigned long long)p.n_roots) {
                     W->unit.root_pos = (int32_t)r;
                     W->unit.depth = 1;
+                    W->unit.lo = 0;
+                    W->unit.hi = -1;
                     W->unit.sub[0] = p.roots[r];
                     kind = 1;
                 } else if (registered && *(volatile int*)&reinterpret_cast<MailHdr*>(my_box)->ready) {
                     __threadfence();
                     gpm_load_cg(&W->unit, reinterpret_cast<const MotifUnit*>(my_box + sizeof(MailHdr)));
+                    *(volatile int*)&reinterpret_cast<MailHdr*>(my_box)->ready = 0;
                     kind = 2;
                 }
             }
@@ -167,54 +172,25 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
             continue;
         }
         idle = false;
+        const unsigned long long t_unit = gpm_globaltimer();
         spin = 0;
 
         // ---------------------------------------------------- set up the unit
+        // (a root, a pre-split range of a root's children, or a donated
+        // range below a replayed path)
         const int root_pos = W->unit.root_pos;
         const int pdepth = W->unit.depth;
         const int root = W->unit.sub[0];
-        if (lane == 0)
-            for (int j = 0; j < pdepth; j++) W->sub[j] = W->unit.sub[j];
-        __syncwarp();
-        mt_setup_prefix(a, W, pdepth, lane);
-        const int32_t* unit_ext;
-        if (kind == 1) {
-            const int lo = mt_root_ext_begin(indptr, indices, root);
-            unit_ext = indices + lo;
-            if (lane == 0) {
-                W->len[1] = indptr[root + 1] - lo;
-                W->cur[1] = 0;
-                W->hi[1] = indptr[root + 1] - lo;
-            }
-        } else if (W->unit.list_off >= 0) {
-            // pre-split seed: the list is a suffix of the root's adjacency
-            unit_ext = indices + W->unit.list_off;
-            if (lane == 0) {
-                W->len[pdepth] = W->unit.len;
-                W->cur[pdepth] = 0;
-                W->hi[pdepth] = W->unit.child_hi;
-            }
-        } else {
-            // donated: copy the list out of this warp's mailbox, then free it
-            int32_t* dst = a.slab + p.lvl_off[pdepth];
-            const int32_t* src = reinterpret_cast<const int32_t*>(my_box + MT_PAYLOAD_OFF);
-            const int len = W->unit.len;
-            for (int t = lane; t < len; t += 32) dst[t] = __ldcg(src + t);
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) {
-                *(volatile int*)&reinterpret_cast<MailHdr*>(my_box)->ready = 0;
-                W->len[pdepth] = len;
-                W->cur[pdepth] = 0;
-                W->hi[pdepth] = W->unit.child_hi;
-            }
-            unit_ext = dst;
+        const int32_t* unit_ext = mt_replay(a, W, lane);
+        if (!unit_ext) {
+            if (lane == 0) atomicCAS(&ctl->error, 0, DEV_EINVAL);
+            aborted = true;
+            break;
         }
-        __syncwarp();
 
         unsigned long long unit_leaves = 0;   // lane-private
-        const bool ok = p.donate ? mt_walk<true>(a, W, pdepth, root, root_pos, unit_ext, sink, unit_leaves, lane)
-                                 : mt_walk<false>(a, W, pdepth, root, root_pos, unit_ext, sink, unit_leaves, lane);
+        const bool ok = p.donate ? mt_walk<true>(a, W, pdepth, root, root_pos, unit_ext, sink, unit_leaves, scanned, lane)
+                                 : mt_walk<false>(a, W, pdepth, root, root_pos, unit_ext, sink, unit_leaves, scanned, lane);
         if (!ok) {
             aborted = true;   // HBM marks are left dirty: the host re-clears them after an error
             break;
@@ -229,9 +205,12 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
             atomicAdd(&ctl->units_done, 1ull);
             atomicAdd((unsigned long long*)&ctl->pending, (unsigned long long)-1ll);
         }
+        busy += gpm_globaltimer() - t_unit;
     }
 
     if (lane == 0 && polls) atomicAdd(&ctl->idle_polls, polls);
+    if (lane == 0) atomicAdd(&ctl->busy_ns, busy);
+    if (lane == 0 && scanned) atomicAdd(&ctl->word_ops, scanned);
     __syncthreads();
     for (int j = threadIdx.x; j < p.npat; j += blockDim.x) {
         const unsigned long long v = bcnt[j];
@@ -244,8 +223,7 @@ __global__ void __launch_bounds__(512) k_motif(MotifParams p) {
 
 // Pre-split seeds: root j of [n_counter, n_counter + n_split) is cut into
 // `chunks` units over equal index ranges of its first extension set
-// ({u in N(r): u > r}, a suffix of N(r)); each unit's list is that suffix from
-// its first child on, by reference into the adjacency array.
+// ({u in N(r): u > r}, a suffix of N(r)).
 __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
                              const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
                              MotifUnit* seeds) {
@@ -262,14 +240,15 @@ __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_coun
     const int L = e - lo;
     for (int c = 0; c < chunks; c++) {
         const long long slot = (long long)j * chunks + c;
-        const int a = (int)((long long)L * c / chunks), z = (int)((long long)L * (c + 1) / chunks);
         MotifUnit u;
         u.root_pos = (int32_t)pos;
         u.depth = 1;
-        u.len = L - a;
-        u.child_hi = z - a;
-        for (int q = 0; q < MT_MAXK; q++) u.sub[q] = q == 0 ? r : -1;
-        u.list_off = lo + a;
+        u.lo = (int)((long long)L * c / chunks);
+        u.hi = (int)((long long)L * (c + 1) / chunks);
+        for (int q = 0; q < MT_MAXK; q++) {
+            u.sub[q] = q == 0 ? r : -1;
+            u.pos[q] = -1;
+        }
         seeds[slot] = u;
     }
 }
@@ -393,7 +372,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.donate = g->cfg.donate;
     unsigned long long cap = 1;
     while (cap < (unsigned long long)nw) cap <<= 1;
-    const size_t stride = (MT_PAYLOAD_OFF + sizeof(int32_t) * MT_LIST + 127) & ~size_t(127);
+    const size_t stride = (sizeof(MailHdr) + sizeof(MotifUnit) + 127) & ~size_t(127);
     const size_t ring_bytes = (sizeof(QSeq) + sizeof(int32_t)) * cap;
     const size_t mbox_bytes = p.donate ? stride * (size_t)nw : 0;
     const size_t seed_bytes = sizeof(MotifUnit) * std::max<unsigned long long>(n_seed, 1);
@@ -438,11 +417,14 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     st.units_done = h.units_done;
     st.donations = h.donations;
     st.idle_polls = h.idle_polls;
+    st.word_ops = h.word_ops;
+    st.busy_warp_ns = h.busy_ns;
     st.kernel_launches = st.grid_blocks ? (n_split > 0 ? 3 : 2) : 0;
     g->stats = st;
     if (h.error) g->mark_bytes_cleared = 0;   // an aborted walk leaves marks behind
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");
     if (h.error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
+    if (h.error >= DEV_ECHECK) fail(GPM_ECUDA, "device consistency check " + std::to_string(h.error - DEV_ECHECK) + " failed");
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
     if (h.overflow) fail(GPM_EOVERFLOW, "a pattern count exceeds 2^64-1");
     for (int j = 0; j < npat; j++) counts_out[j] = host[j];
@@ -620,6 +602,7 @@ static void motif_count_noalloc(const int32_t* indptr, const int32_t* indices, i
     GPM_CUDA(cudaMemcpyAsync(host, dcounts, sizeof(unsigned long long) * npat, cudaMemcpyDeviceToHost, s));
     GPM_CUDA(cudaStreamSynchronize(s));
     if (h.error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
+    if (h.error >= DEV_ECHECK) fail(GPM_ECUDA, "device consistency check " + std::to_string(h.error - DEV_ECHECK) + " failed");
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
     if (h.overflow) fail(GPM_EOVERFLOW, "a pattern count exceeds 2^64-1");
     for (int j = 0; j < npat; j++) counts[j] = host[j];

@@ -31,18 +31,20 @@
 namespace gpm {
 
 constexpr int MT_MAXK = GPM_MOTIF_MAX_K;
-constexpr int MT_LIST = 1024;                  // entries carried by one donated unit
 constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns
-constexpr int MT_PAYLOAD_OFF = 64;             // payload offset inside a mailbox (after MailHdr + MotifUnit)
 
+// A work unit: the children at positions [lo, hi) of the extension array of
+// the node tr = (sub[0], .., sub[depth-1]) (hi < 0: all of them).  The node's
+// array is rebuilt by the receiving warp by replaying the path: tr[j] is the
+// entry at position pos[j] of ext_j (1 <= j < depth), and ESU's arrays are a
+// deterministic function of those choices -- so a unit is a few dozen bytes
+// whatever the length of its array.
 struct MotifUnit {
     int32_t root_pos;
-    int32_t depth;              // |tr| of the donated node
-    int32_t len;                // entries in its list (the node's extension-array suffix)
-    int32_t child_hi;           // children to expand: list positions [0, child_hi)
+    int32_t depth;
+    int32_t lo, hi;
     int32_t sub[MT_MAXK];
-    int32_t list_off;           // >= 0: the list is indices[list_off ..] (a root's own
-                                // extension set); < 0: it is the queue slot's payload
+    int32_t pos[MT_MAXK];
 };
 static_assert(sizeof(MotifUnit) % 4 == 0, "unit must be word-sized");
 
@@ -67,8 +69,7 @@ struct MotifWalk {
     int32_t* slab;              // this warp's extension arrays
     const long long* lvl_off;   // start of ext_l inside the slab (k-1 entries used)
     // donation (DONATE only): ring of idle warp ids and the warps' mailboxes
-    // (mailbox of warp w at mbox + w * mbox_stride: MailHdr, MotifUnit, then
-    // MT_LIST payload ints at MT_PAYLOAD_OFF)
+    // (mailbox of warp w at mbox + w * mbox_stride: MailHdr, then MotifUnit)
     Control* ctl;
     QSeq* ring_seq;
     int32_t* ring_ids;
@@ -108,17 +109,24 @@ __device__ __forceinline__ void mt_count_leaves(Sink& sink, bool active, int pid
 
 // First position in the sorted N(v) holding a vertex above `root`.  Sets
 // rooted at `root` hold no smaller vertex, so neither their marks nor their
-// extensions ever look below it: every adjacency scan starts here.  Short
-// lists are scanned whole (a search would cost more than it skips).
+// extensions ever look below it: every adjacency scan starts here.  Found by
+// the whole warp (every lane must call): 32 evenly spaced probes narrow the
+// range 32-fold per round, so a list of up to 1,024 entries needs two rounds
+// of independent loads instead of a chain of ten dependent ones.
 __device__ __forceinline__ int mt_above(const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
-                                        int v, int root) {
+                                        int v, int root, int lane) {
     int lo = indptr[v], hi = indptr[v + 1];
-    if (hi - lo <= 64) return lo;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (indices[mid] <= root) lo = mid + 1; else hi = mid;
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) >> 5;
+        const int p = lo + lane * step;
+        const int c = __popc(__ballot_sync(GPM_FULL_MASK, p < hi && indices[p] <= root));
+        if (c == 0) return lo;                  // indices[lo] > root
+        const int nlo = lo + (c - 1) * step + 1;  // indices[nlo - 1] <= root
+        hi = min(hi, lo + c * step);              // indices[hi] > root, or hi is the end
+        lo = nlo;
     }
-    return lo;
+    const int p = lo + lane;
+    return lo + __popc(__ballot_sync(GPM_FULL_MASK, p < hi && indices[p] <= root));
 }
 
 // Marks and traversal codes of a unit's prefix tr[0..pdepth-1] (W->sub).
@@ -128,7 +136,7 @@ __device__ __forceinline__ void mt_setup_prefix(const MotifWalk& a, MtWarp* W, i
     const int root = W->sub[0];
     for (int j = 0; j < pdepth; j++) {
         const int v = W->sub[j];
-        for (int t = mt_above(a.indptr, a.indices, v, root) + lane; t < a.indptr[v + 1]; t += 32)
+        for (int t = mt_above(a.indptr, a.indices, v, root, lane) + lane; t < a.indptr[v + 1]; t += 32)
             a.mk[a.indices[t] - a.mbase] |= (unsigned char)(1u << j);
         __syncwarp();
     }
@@ -148,7 +156,7 @@ __device__ __forceinline__ void mt_clear_prefix(const MotifWalk& a, MtWarp* W, i
     const int root = W->sub[0];
     for (int j = 0; j < pdepth; j++) {
         const int v = W->sub[j];
-        for (int t = mt_above(a.indptr, a.indices, v, root) + lane; t < a.indptr[v + 1]; t += 32)
+        for (int t = mt_above(a.indptr, a.indices, v, root, lane) + lane; t < a.indptr[v + 1]; t += 32)
             a.mk[a.indices[t] - a.mbase] = 0;
         __syncwarp();
     }
@@ -156,23 +164,165 @@ __device__ __forceinline__ void mt_clear_prefix(const MotifWalk& a, MtWarp* W, i
     __syncwarp();
 }
 
-// First extension set of root r: the suffix of the sorted N(r) above r.
+// First extension set of root r: the suffix of the sorted N(r) above r
+// (warp-wide, like mt_above).
 __device__ __forceinline__ int mt_root_ext_begin(const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
-                                                 int r) {
-    int lo = indptr[r], hi = indptr[r + 1];
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (indices[mid] <= r) lo = mid + 1; else hi = mid;
+                                                 int r, int lane) {
+    return mt_above(indptr, indices, r, r, lane);
+}
+
+// Traversal code of tr + w for a child w at depth l (its bits against
+// tr[0..l-1] come from the marks).
+__device__ __forceinline__ int mt_child_code(const MotifWalk& a, const MtWarp* W, int l, int w) {
+    const int sigw = a.mk[w - a.mbase] & ((1 << l) - 1);
+    return l >= 2 ? (W->code[l] | (sigw << mt_code_off(l))) : 0;
+}
+
+// Push child w = ext[c] of depth l: ext_{l+1} = ext[c+1 .. len) followed by
+// the exclusive neighbours of w (above the root, unmarked by tr[0..l-1] and
+// not in tr), and N(w) is marked with bit l.  wb..we: N(w) above the root.
+__device__ __forceinline__ bool mt_push(const MotifWalk& a, MtWarp* W, int l, int c, const int32_t* ext, int w,
+                                        int wb, int we, int codew, int lane) {
+    int32_t* nxt = a.slab + a.lvl_off[l + 1];
+    const int len = W->len[l];
+    const int inh = len - (c + 1);
+    if ((long long)inh + (we - wb) > a.lvl_off[l + 2] - a.lvl_off[l + 1]) {   // never, by the level sizes
+        if (lane == 0) atomicCAS(a.err, 0, DEV_ECHECK + 5);
+        return false;
     }
-    return lo;
+    for (int t = lane; t < inh; t += 32) nxt[t] = ext[c + 1 + t];
+    const unsigned char low = (unsigned char)(0x80 | ((1u << l) - 1));
+    int n_new = inh;
+    for (int t0 = wb; t0 < we; t0 += 32) {
+        const int t = t0 + lane;
+        bool ex = false;
+        int x = 0;
+        if (t < we) {
+            x = a.indices[t];
+            const unsigned char m = a.mk[x - a.mbase];
+            ex = (m & low) == 0;
+            a.mk[x - a.mbase] = m | (unsigned char)(1u << l);
+        }
+        const unsigned bal = __ballot_sync(GPM_FULL_MASK, ex);
+        if (ex) nxt[n_new + __popc(bal & gpm_lanemask_lt())] = x;
+        n_new += __popc(bal);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        a.mk[w - a.mbase] |= 0x80;
+        W->sub[l] = w;
+        W->code[l + 1] = codew;
+        W->len[l + 1] = n_new;
+        W->cur[l + 1] = 0;
+        W->hi[l + 1] = n_new;
+    }
+    __syncwarp();
+    return true;
+}
+
+// Set up unit u (in W->unit): marks and array of the root, then the path
+// replayed push by push; levels above the unit's own are left exhausted
+// (cur = hi = the chosen position + 1).  Returns the array of the unit's
+// node, or nullptr if the path does not match the graph (device error).
+__device__ __forceinline__ const int32_t* mt_replay(const MotifWalk& a, MtWarp* W, int lane) {
+    const int root = W->unit.sub[0];
+    const int depth = W->unit.depth;
+    if (depth < 1 || depth > max(a.k - 2, 1)) {
+        if (lane == 0) atomicCAS(a.err, 0, DEV_ECHECK + 3);
+        return nullptr;
+    }
+    if (lane == 0) W->sub[0] = root;
+    __syncwarp();
+    mt_setup_prefix(a, W, 1, lane);
+    const int b = mt_root_ext_begin(a.indptr, a.indices, root, lane);
+    const int32_t* ext = a.indices + b;
+    if (lane == 0) W->len[1] = a.indptr[root + 1] - b;
+    __syncwarp();
+    for (int l = 1; l < depth; l++) {
+        const int c = W->unit.pos[l];
+        if (c < 0 || c >= W->len[l]) {
+            if (lane == 0) atomicCAS(a.err, 0, DEV_ECHECK + 1);
+            return nullptr;
+        }
+        const int w = ext[c];
+        if (w != W->unit.sub[l]) {
+            if (lane == 0) atomicCAS(a.err, 0, DEV_ECHECK + 2);
+            return nullptr;
+        }
+        const int codew = mt_child_code(a, W, l, w);
+        const int wb = mt_above(a.indptr, a.indices, w, root, lane), we = a.indptr[w + 1];
+        if (!mt_push(a, W, l, c, ext, w, wb, we, codew, lane)) return nullptr;
+        if (lane == 0) {
+            W->cur[l] = c + 1;
+            W->hi[l] = c + 1;
+        }
+        ext = a.slab + a.lvl_off[l + 1];
+    }
+    if (W->unit.lo < 0 || W->unit.lo > W->len[depth]) {
+        if (lane == 0) atomicCAS(a.err, 0, DEV_ECHECK + 6);
+        return nullptr;
+    }
+    if (lane == 0) {
+        W->cur[depth] = W->unit.lo;
+        W->hi[depth] = W->unit.hi < 0 ? W->len[depth] : min(W->unit.hi, W->len[depth]);
+    }
+    __syncwarp();
+    return ext;
+}
+
+// Split point of children [from, to) of a node whose array has len entries:
+// a child's subtree grows about like (len - c)^e (e = levels below it), so
+// [from, mid) and [mid, to) carry about the same work when
+// (len - mid)^(e+1) is the mean of (len - from)^(e+1) and (len - to)^(e+1).
+__device__ __forceinline__ int mt_split(int from, int to, int len, int e) {
+    const float A = (float)(len - from), B = (float)(len - to);
+    const float q = (float)(e + 1);
+    const float m = __powf(0.5f * (__powf(A, q) + __powf(fmaxf(B, 1.0f), q)), 1.0f / q);
+    const int mid = len - (int)ceilf(m);
+    return max(from + 1, min(mid, to - 1));
+}
+
+// Hand the later children of the shallowest splittable level to a
+// registered idle warp (lane 0 only; a cold path, kept out of line).  The
+// split balances estimated work; the unit carries the path, not the array.
+__device__ __noinline__ static void mt_donate(Control* ctl, QSeq* ring_seq, int32_t* ring_ids,
+                                              unsigned long long ring_cap, unsigned char* mbox, int mbox_stride,
+                                              int donate_min, int k, MtWarp* W, int pdepth, int l, int root_pos) {
+    for (int t = pdepth; t <= l; t++) {
+        const int from = W->cur[t], to = W->hi[t];
+        if (to - from < max(donate_min, 2)) continue;
+        const int mid = mt_split(from, to, W->len[t], k - 1 - t);
+        int wid;
+        if (!gpm_idle_claim(ring_seq, ring_ids, ring_cap, &ctl->q_head, &wid)) return;
+        if (wid < 0 || (unsigned long long)wid >= ring_cap) {   // never: ids are registered warps
+            atomicCAS(&ctl->error, 0, DEV_ECHECK + 4);
+            return;
+        }
+        unsigned char* box = mbox + (size_t)wid * mbox_stride;
+        MotifUnit* u = reinterpret_cast<MotifUnit*>(box + sizeof(MailHdr));
+        u->root_pos = root_pos;
+        u->depth = t;
+        u->lo = mid;
+        u->hi = to;
+        for (int z = 0; z < MT_MAXK; z++) {
+            u->sub[z] = z < t ? W->sub[z] : -1;
+            u->pos[z] = (z >= 1 && z < t) ? W->cur[z] - 1 : -1;
+        }
+        W->hi[t] = mid;
+        atomicAdd((unsigned long long*)&ctl->pending, 1ull);
+        __threadfence();
+        atomicExch(&reinterpret_cast<MailHdr*>(box)->ready, 1);
+        atomicAdd(&ctl->donations, 1ull);
+        return;
+    }
 }
 
 // Walk the unit whose node is at depth pdepth (W->cur/hi/len[pdepth] set,
 // unit_ext = its extension array).  Returns false if it stopped on a device
 // error (marks are then left dirty).  unit_leaves: lane-private leaf count.
 template <bool DONATE, class Sink>
-__device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int root_pos, const int32_t* unit_ext,
-                        Sink& sink, unsigned long long& unit_leaves, int lane) {
+__device__ __forceinline__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int root_pos, const int32_t* unit_ext,
+                        Sink& sink, unsigned long long& unit_leaves, unsigned long long& scanned, int lane) {
     const int k = a.k;
     int l = pdepth;
     int iter = 0;
@@ -183,7 +333,9 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
             if (l == pdepth) break;
             // pop tr[l-1] (pushed at depth l-1)
             const int w = W->sub[l - 1];
-            for (int t = mt_above(a.indptr, a.indices, w, root) + lane; t < a.indptr[w + 1]; t += 32)
+            const int wb = mt_above(a.indptr, a.indices, w, root, lane), we = a.indptr[w + 1];
+            if (lane == 0) scanned += (unsigned)(we - wb);
+            for (int t = wb + lane; t < we; t += 32)
                 a.mk[a.indices[t] - a.mbase] &= (unsigned char)~(1u << (l - 1));
             __syncwarp();
             if (lane == 0) a.mk[w - a.mbase] &= 0x7f;
@@ -193,19 +345,21 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
         }
         const int32_t* ext = l == pdepth ? unit_ext : a.slab + a.lvl_off[l];
         const int w = ext[c];
+        __syncwarp();                       // every lane has read cur[l] before it moves on
         if (lane == 0) W->cur[l] = c + 1;
-        const int sigw = a.mk[w - a.mbase] & ((1 << l) - 1);
-        const int codew = l >= 2 ? (W->code[l] | (sigw << mt_code_off(l))) : 0;
-        const int wb = mt_above(a.indptr, a.indices, w, root), we = a.indptr[w + 1];
+        const int codew = mt_child_code(a, W, l, w);
+        const int wb = mt_above(a.indptr, a.indices, w, root, lane), we = a.indptr[w + 1];
+        if (lane == 0 && l + 1 != k - 1) scanned += (unsigned)(we - wb);
         const unsigned char low = (unsigned char)(0x80 | ((1u << l) - 1));
         if (l + 1 == k - 1) {
             // ---- last level: leaves of the (k-1)-set tr + w
             const int offk = mt_code_off(l + 1);
+            if (lane == 0) scanned += 2ull * (unsigned)(we - wb);
             int excl = 0;
             for (int t = wb + lane; t < we; t += 32) {
                 const int x = a.indices[t];
                 const unsigned char m = a.mk[x - a.mbase];
-                excl += (x > root && (m & low) == 0) ? 1 : 0;
+                excl += (m & low) == 0 ? 1 : 0;
                 a.mk[x - a.mbase] = m | (unsigned char)(1u << l);
             }
             excl = __reduce_add_sync(GPM_FULL_MASK, (unsigned)excl);
@@ -235,39 +389,13 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
             __syncwarp();
         } else {
             // ---- push w: ext_{l+1} = ext_l[c+1:] ++ exclusive neighbours of w
-            int32_t* nxt = a.slab + a.lvl_off[l + 1];
-            const int len = W->len[l];
-            const int inh = len - (c + 1);
-            for (int t = lane; t < inh; t += 32) nxt[t] = ext[c + 1 + t];
-            int n_new = inh;
-            for (int t0 = wb; t0 < we; t0 += 32) {
-                const int t = t0 + lane;
-                bool ex = false;
-                int x = 0;
-                if (t < we) {
-                    x = a.indices[t];
-                    const unsigned char m = a.mk[x - a.mbase];
-                    ex = x > root && (m & low) == 0;
-                    a.mk[x - a.mbase] = m | (unsigned char)(1u << l);
-                }
-                const unsigned bal = __ballot_sync(GPM_FULL_MASK, ex);
-                if (ex) nxt[n_new + __popc(bal & gpm_lanemask_lt())] = x;
-                n_new += __popc(bal);
-            }
-            __syncwarp();
-            if (lane == 0) {
-                a.mk[w - a.mbase] |= 0x80;
-                W->sub[l] = w;
-                W->code[l + 1] = codew;
-                W->len[l + 1] = n_new;
-                W->cur[l + 1] = 0;
-                W->hi[l + 1] = n_new;
-            }
-            __syncwarp();
+            if (!mt_push(a, W, l, c, ext, w, wb, we, codew, lane)) return false;
             l++;
         }
 
-        if (DONATE && (++iter & 7) == 0) {
+        // donation check: every 8 steps, and after every last-level child
+        // (each of which can be long)
+        if (DONATE && ((++iter & 7) == 0 || l + 1 == k - 1)) {
             Control* ctl = a.ctl;
             int err = 0, want = 0;
             if (lane == 0) {
@@ -281,46 +409,10 @@ __device__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdepth, int root, int
             err = __shfl_sync(GPM_FULL_MASK, err, 0);
             if (err) return false;
             want = __shfl_sync(GPM_FULL_MASK, want, 0);
-            if (want) {
-                // shallowest level with enough unexpanded children: give away the
-                // upper half (its list suffix travels in the receiver's mailbox)
-                for (int t = pdepth; t <= l; t++) {
-                    const int from = W->cur[t], to = W->hi[t], len = W->len[t];
-                    const int rem = to - from;
-                    if (rem < max(a.donate_min, 2)) continue;
-                    int start = from + (rem - rem / 2);
-                    start = max(start, len - MT_LIST);
-                    if (start >= to) continue;
-                    int wid = -1;
-                    if (lane == 0 && !gpm_idle_claim(a.ring_seq, a.ring_ids, a.ring_cap, &ctl->q_head, &wid)) wid = -1;
-                    wid = __shfl_sync(GPM_FULL_MASK, wid, 0);
-                    if (wid < 0) break;
-                    unsigned char* box = a.mbox + (size_t)wid * a.mbox_stride;
-                    int32_t* dst = reinterpret_cast<int32_t*>(box + MT_PAYLOAD_OFF);
-                    const int32_t* src = t == pdepth ? unit_ext : a.slab + a.lvl_off[t];
-                    for (int z = start + lane; z < len; z += 32) dst[z - start] = src[z];
-                    if (lane == 0) {
-                        MotifUnit u;
-                        u.root_pos = root_pos;
-                        u.depth = t;
-                        u.len = len - start;
-                        u.child_hi = to - start;
-                        for (int z = 0; z < MT_MAXK; z++) u.sub[z] = z < t ? W->sub[z] : -1;
-                        u.list_off = -1;
-                        *reinterpret_cast<MotifUnit*>(box + sizeof(MailHdr)) = u;
-                        W->hi[t] = start;
-                        atomicAdd((unsigned long long*)&ctl->pending, 1ull);
-                    }
-                    __threadfence();
-                    __syncwarp();
-                    if (lane == 0) {
-                        atomicExch(&reinterpret_cast<MailHdr*>(box)->ready, 1);
-                        atomicAdd(&ctl->donations, 1ull);
-                    }
-                    __syncwarp();
-                    break;
-                }
-            }
+            if (want && lane == 0)
+                mt_donate(ctl, a.ring_seq, a.ring_ids, a.ring_cap, a.mbox, a.mbox_stride, a.donate_min, k, W, pdepth,
+                          l, root_pos);
+            __syncwarp();
         }
     }
     return true;

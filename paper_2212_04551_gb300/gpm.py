@@ -44,14 +44,16 @@ class gpm_config(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("donate_min", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
-                ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32)]
+                ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32),
+                ("clique_compact", ctypes.c_int32)]
 
 
 class gpm_stats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("units_done", ctypes.c_uint64),
                 ("donations", ctypes.c_uint64), ("idle_polls", ctypes.c_uint64),
                 ("grid_blocks", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("word_ops", ctypes.c_uint64), ("kernel_launches", ctypes.c_int32)]
+                ("word_ops", ctypes.c_uint64), ("kernel_launches", ctypes.c_int32),
+                ("busy_warp_ns", ctypes.c_uint64)]
 
 
 _lib = None
@@ -261,10 +263,18 @@ def gpm_set_config(g: Graph, cfg: gpm_config | None = None, **kw) -> None:
     _check(load().gpm_set_config(g, ctypes.byref(c)), "gpm_set_config")
 
 
+def _stats_dict(s: gpm_stats) -> dict:
+    d = {f: getattr(s, f) for f, _ in gpm_stats._fields_}
+    slots = d["grid_blocks"] * d["warps_per_block"] * d["kernel_ms"] * 1e6
+    # fraction of the grid's warp-time spent without a work unit
+    d["idle_warp_frac"] = max(0.0, 1.0 - d["busy_warp_ns"] / slots) if slots > 0 else None
+    return d
+
+
 def gpm_get_stats(g: Graph) -> dict:
     s = gpm_stats()
     _check(load().gpm_get_stats(g, ctypes.byref(s)), "gpm_get_stats")
-    return {f: getattr(s, f) for f, _ in gpm_stats._fields_}
+    return _stats_dict(s)
 
 
 def gpm_last_error() -> str:
@@ -423,7 +433,7 @@ def gpm_batch_set_config(b: Batch, **kw) -> None:
 def gpm_batch_get_stats(b: Batch) -> dict:
     s = gpm_stats()
     _check(load().gpm_batch_get_stats(b, ctypes.byref(s)), "gpm_batch_get_stats")
-    return {f: getattr(s, f) for f, _ in gpm_stats._fields_}
+    return _stats_dict(s)
 
 
 def batch_from_graphs(graph_list, stream=None) -> Batch:

@@ -112,6 +112,45 @@ def test_turan_and_union():
         assert gpm.gpm_clique_count(dg, k) == e[k]
 
 
+def _turan_cliques(parts, k):
+    e = [1] + [0] * k
+    for x in parts:
+        for j in range(k, 0, -1):
+            e[j] += e[j - 1] * x
+    return e[k]
+
+
+@functools.lru_cache(maxsize=1)
+def _dense_reference():
+    """Dense G(n, p) graphs (oriented out-degrees up to ~100: 3-4 words per
+    bitmap row) with their oracle clique counts for k = 4, 5, 6."""
+    out = []
+    for seed, (n, p) in enumerate([(180, 0.5), (160, 0.6)]):
+        g = G.gnp(n, p, 900 + seed)
+        out.append((g, [O.clique_count(g, k) for k in (4, 5, 6)]))
+    return out
+
+
+@pytest.mark.parametrize("compact", [0, 1, 2])
+def test_compacted_tail_dense_graphs(compact):
+    """The two-level tail on the node's own members (clique_compact) against
+    closed forms (K_n, Turan) and the oracle on dense random graphs whose
+    oriented out-degrees need three to six words per bitmap row."""
+    for n in (97, 150):
+        dg = gpm.graph_from_csr(G.complete(n))
+        gpm.gpm_set_config(dg, clique_compact=compact)
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 7)] == [comb(n, k) for k in range(4, 8)]
+    dg = gpm.graph_from_csr(G.turan(200, 10))
+    gpm.gpm_set_config(dg, clique_compact=compact, clique_tail=2)
+    assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 7)] == [_turan_cliques([20] * 10, k)
+                                                                     for k in range(4, 8)]
+    for g, want in _dense_reference():
+        dg = gpm.graph_from_csr(g)
+        gpm.gpm_set_config(dg, clique_compact=compact)
+        assert [gpm.gpm_clique_count(dg, k) for k in (4, 5, 6)] == want, g.n
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 6)] == want, g.n
+
+
 def test_star_with_large_hub():
     """A hub of degree 300 (motifs) -- a long exclusive list in one step."""
     g = G.star(300)
@@ -168,7 +207,8 @@ def _schedule_reference():
 @pytest.mark.parametrize("cfg", [
     dict(donate=0), dict(donate=1, donate_min=2, donate_after_us=0), dict(warps_per_block=4),
     dict(warps_per_block=16, blocks_per_sm=1), dict(order=gpm.GPM_ORDER_ID),
-    dict(warps_per_block=1, blocks_per_sm=1), dict(clique_tail=2), dict(clique_tail=3, warps_per_block=2)])
+    dict(warps_per_block=1, blocks_per_sm=1), dict(clique_tail=2), dict(clique_tail=3, warps_per_block=2),
+    dict(clique_compact=1), dict(clique_compact=2)])
 def test_schedule_never_changes_counts(cfg):
     g, ref_c, ref_m = _schedule_reference()
     dg = gpm.graph_from_csr(g)
