@@ -85,8 +85,10 @@ def kernel_source_hash(names) -> str:
 
 
 def profiled_traffic(summary: str, src_hash: str, units_now: float):
-    """DRAM bytes per launch from a committed ncu summary, scaled to this
-    launch's units, or None when the kernel source changed since."""
+    """DRAM bytes per launch from a committed ncu summary of the same launch,
+    or None when the kernel source changed since or the launch differs (the
+    clique kernel's DRAM bytes are the per-root row builds, which do not grow
+    with the word operations of deeper k ranges, so they are not scaled)."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
@@ -102,7 +104,7 @@ def profiled_traffic(summary: str, src_hash: str, units_now: float):
         u = float(kv["units_per_launch"])
     except (KeyError, ValueError):
         return None
-    return t * (units_now / u) if u > 0 else None
+    return t if u > 0 and abs(units_now - u) <= 1e-6 * u else None
 
 
 class ClockSampler:

@@ -316,7 +316,7 @@ gpm_status gpm_batch_get_stats(const gpm_batch* b, gpm_stats* out);
  * motif kernel with work donation off.  The call allocates nothing: it calls
  * no cudaMalloc or cudaFree and no allocating library routine; its scratch
  * (control block, counters, validation flags, root list, pattern table) is
- * one file-scope device array of 2,138,624 bytes that every device loading
+ * one file-scope device array of 2,139,392 bytes that every device loading
  * the library holds until the process exits.
  *
  *   indptr, indices : DEVICE pointers to the undirected CSR (conventions of

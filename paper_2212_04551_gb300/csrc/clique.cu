@@ -123,6 +123,7 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     unsigned long long idle_since = 0;
     unsigned long long busy = 0;      // time spent inside work units (%globaltimer ns)
     bool aborted = false;
+    bool exhausted = false;           // lane 0: no seeds or roots left
 
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // this warp's global id
     MailHdr* my_box = reinterpret_cast<MailHdr*>(p.mbox + (size_t)gw * p.mbox_stride);
@@ -133,14 +134,16 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         // ---- acquire a unit: pre-split seeds, then roots, then donated work
         int kind = 0;
         if (lane == 0) {
-            unsigned long long sd = *(volatile unsigned long long*)&ctl->next_seed;
+            // seeds and roots only run out once: after that, look at the mailbox alone
+            unsigned long long sd = exhausted ? ~0ull : *(volatile unsigned long long*)&ctl->next_seed;
             if (sd < (unsigned long long)p.n_seeds) sd = atomicAdd(&ctl->next_seed, 1ull);
             if (sd < (unsigned long long)p.n_seeds) {
                 *unit = p.seeds[sd];
                 kind = 3;
             } else {
-                unsigned long long r = *(volatile unsigned long long*)&ctl->next_root;
+                unsigned long long r = exhausted ? ~0ull : *(volatile unsigned long long*)&ctl->next_root;
                 if (r < (unsigned long long)p.n_roots) r = atomicAdd(&ctl->next_root, 1ull);
+                if (r >= (unsigned long long)p.n_roots) exhausted = true;
                 if (r < (unsigned long long)p.n_roots) {
                     unit->root_pos = (int32_t)r;
                     unit->depth = 0;
@@ -172,20 +175,25 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
                 if (lane == 0) ok = gpm_idle_register(p.ring_seq, p.ring_ids, p.ring_cap, &ctl->q_tail, gw) ? 1 : 0;
                 registered = __shfl_sync(GPM_FULL_MASK, ok, 0) != 0;
             }
-            long long pend = 0;
-            int err = 0;
-            if (lane == 0) {
-                pend = *(volatile long long*)&ctl->pending;
-                err = *(volatile int*)&ctl->error;
+            // the termination state is shared by every idle warp: look at it
+            // every 16th spin only (the own mailbox is checked every spin)
+            if ((polls & 15) == 0) {
+                long long pend = 0;
+                int err = 0;
+                if (lane == 0) {
+                    pend = *(volatile long long*)&ctl->pending;
+                    err = *(volatile int*)&ctl->error;
+                }
+                pend = __shfl_sync(GPM_FULL_MASK, pend, 0);
+                err = __shfl_sync(GPM_FULL_MASK, err, 0);
+                if (pend <= 0 || err) break;
+                if (pend != last_pending) {
+                    last_pending = pend;
+                    idle_since = gpm_globaltimer();
+                }
             }
-            pend = __shfl_sync(GPM_FULL_MASK, pend, 0);
-            err = __shfl_sync(GPM_FULL_MASK, err, 0);
-            if (pend <= 0 || err) break;
             const unsigned long long now = gpm_globaltimer();
-            if (pend != last_pending) {
-                last_pending = pend;
-                idle_since = now;
-            } else if (now - idle_since > p.max_idle_ns) {
+            if (now - idle_since > p.max_idle_ns) {
                 if (lane == 0) atomicCAS(&ctl->error, 0, DEV_ETIMEOUT);
                 break;
             }

@@ -63,10 +63,17 @@ __host__ __device__ inline int cq_tri_words(int d, int w) {
     return 32 * (b * w - b * (b - 1) / 2) + (d - 32 * b) * (w - b);
 }
 
+// row(p) = base + cq_tri_words(p, w) - p / 32, which simplifies to
+// base + p (w - b) + b (16 b + 15) with b = p / 32.
+__host__ __device__ inline int cq_tri_row(int p, int w) {
+    const int b = p >> 5;
+    return p * (w - b) + b * (16 * b + 15);
+}
+
 struct TriRows {                    // the root-local matrix
     const uint32_t* base;
     int w;
-    __device__ __forceinline__ const uint32_t* row(int p) const { return base + cq_tri_words(p, w) - (p >> 5); }
+    __device__ __forceinline__ const uint32_t* row(int p) const { return base + cq_tri_row(p, w); }
 };
 
 struct RectRows {                   // a plain row-major matrix (the compacted one)
@@ -162,7 +169,7 @@ __device__ __noinline__ static void build_rows(const int32_t* __restrict__ off, 
     for (int i = 0; i < d; i++) {
         const int u = list[i];
         const int ub = off[u], du = outdeg[u];
-        uint32_t* row = rows + cq_tri_words(pos[i], w) - (pos[i] >> 5);   // words >= pos[i] / 32
+        uint32_t* row = rows + cq_tri_row(pos[i], w);   // words >= pos[i] / 32
         for (int t = lane; t < du; t += 32) {
             const int x = adj[ub + t];
             if (x < first || x > last) continue;
@@ -234,12 +241,12 @@ __device__ __forceinline__ int cq_compact(const uint32_t* C, int w, int from, in
 template <int W, class Rows>
 __device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const Rows& rows, int w) {
     unsigned acc = 0;
-    for (int q = 0; q < w; q++) {
-        // word q of x without dynamic register indexing
-        uint32_t bits = 0;
+    // the word loop is unrolled, so for the bits of word q the row words
+    // below q (zero) are skipped at compile time
 #pragma unroll
-        for (int z = 0; z < W; z++)
-            if (z == q) bits = x[z];
+    for (int q = 0; q < W; q++) {
+        if (q >= w) break;
+        uint32_t bits = x[q];
         while (bits) {
             const int l1 = 32 * q + __ffs(bits) - 1;
             bits &= bits - 1u;
@@ -250,16 +257,16 @@ __device__ __forceinline__ unsigned cq_sum_rows(const uint32_t (&x)[W], const Ro
                 const uint32_t* r2 = rows.row(l2);
                 uint32_t a[W], b[W];
 #pragma unroll
-                for (int z = 0; z < W; z++) {
-                    a[z] = (z >= q && z < w) ? r1[z] : 0u;
-                    b[z] = (z >= q && z < w) ? r2[z] : 0u;
+                for (int z = q; z < W; z++) {
+                    a[z] = z < w ? r1[z] : 0u;
+                    b[z] = z < w ? r2[z] : 0u;
                 }
 #pragma unroll
-                for (int z = 0; z < W; z++) acc += __popc(x[z] & a[z]) + __popc(x[z] & b[z]);
+                for (int z = q; z < W; z++) acc += __popc(x[z] & a[z]) + __popc(x[z] & b[z]);
             } else {
 #pragma unroll
-                for (int z = 0; z < W; z++)
-                    if (z >= q && z < w) acc += __popc(x[z] & r1[z]);
+                for (int z = q; z < W; z++)
+                    if (z < w) acc += __popc(x[z] & r1[z]);
             }
         }
     }

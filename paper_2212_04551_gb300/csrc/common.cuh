@@ -124,20 +124,26 @@ namespace gpm {
 
 // --------------------------------------------------------- shared control
 
-// Control block of one persistent enumeration launch (device memory).
-struct Control {
-    unsigned long long counts[GPM_CLIQUE_MAX_K + 1];  // per clique size (clique kernel)
+// Control block of one persistent enumeration launch (device memory).  The
+// words that different groups of warps hammer sit on separate 128-byte
+// lines: unit counters (warps taking work), termination state (polled by
+// idle warps), the idle-ring positions (read by busy warps deciding to
+// split), statistics, and the final counts.
+struct alignas(128) Control {
     unsigned long long next_root;     // next index into the root list
-    long long pending;                // roots + donated units not yet finished
-    int idle;                         // warps currently without work
-    int error;                        // GPM_* status raised on the device
-    unsigned long long q_head, q_tail;
-    unsigned long long donations, units_done, idle_polls;
-    unsigned long long word_ops;      // clique: 32-bit candidate-word AND+POPC operations
     unsigned long long next_seed;     // next pre-split seed unit
+    alignas(128) long long pending;   // roots + donated units not yet finished
+    int error;                        // GPM_* status raised on the device
+    int idle;                         // (unused)
+    alignas(128) unsigned long long q_head;   // (alignas binds per declarator: one per line)
+    unsigned long long q_tail;
+    alignas(128) unsigned long long donations;
+    unsigned long long units_done, idle_polls;
+    unsigned long long word_ops;      // clique: 32-bit candidate-word AND+POPC operations
     unsigned long long busy_ns;       // sum over warps of time spent inside work units
     int overflow;
     int pad;
+    alignas(128) unsigned long long counts[GPM_CLIQUE_MAX_K + 1];  // per clique size (clique kernel)
 };
 
 // Device-side status values (mirrors gpm_status).
@@ -189,7 +195,8 @@ void order_by_score(gpm_graph* g, const float* d_score, const int32_t* d_roots, 
 
 // helpers
 int resident_blocks(const void* kernel, int threads, size_t smem);
-Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block);
+// max_per_sm > 0 caps the resident blocks per SM unless the configuration sets blocks_per_sm
+Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block, int max_per_sm = 0);
 // warps per block (16, 8, 4, 2 or 1) that keeps the most warps resident per SM
 int best_warps_per_block(const void* kernel, size_t smem_per_warp, size_t smem_fixed);
 gpm_config default_config();

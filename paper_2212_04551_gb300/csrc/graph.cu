@@ -497,13 +497,14 @@ int best_warps_per_block(const void* kernel, size_t smem_per_warp, size_t smem_f
     return best;
 }
 
-Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block) {
+Grid plan_grid(gpm_graph* g, const void* kernel, int warps_per_block, size_t smem_per_block, int max_per_sm) {
     Grid gr;
     gr.warps_per_block = warps_per_block;
     int per_sm = resident_blocks(kernel, warps_per_block * 32, smem_per_block);
     if (per_sm <= 0) fail(GPM_EINVAL, "kernel cannot be resident with this configuration (shared memory "
                                       + std::to_string(smem_per_block) + " B)");
     if (g->cfg.blocks_per_sm > 0) per_sm = std::min(per_sm, g->cfg.blocks_per_sm);
+    else if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
     gr.blocks = per_sm * g->num_sms;
     return gr;
 }

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     unsigned long long idle_since = 0;
     unsigned long long busy = 0;      // time spent inside work units (%globaltimer ns)
     bool aborted = false;
+    bool exhausted = false;           // lane 0: no seeds or roots left
 
     unsigned char* my_box = p.mbox ? p.mbox + (size_t)gw * p.mbox_stride : nullptr;
     bool registered = false;
@@ -110,14 +111,16 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         // ---- acquire a unit: pre-split seeds, then roots, then donated work
         int kind = 0;
         if (lane == 0) {
-            unsigned long long sd = *(volatile unsigned long long*)&ctl->next_seed;
+            // seeds and roots only run out once: after that, look at the mailbox alone
+            unsigned long long sd = exhausted ? ~0ull : *(volatile unsigned long long*)&ctl->next_seed;
             if (sd < (unsigned long long)p.n_seeds) sd = atomicAdd(&ctl->next_seed, 1ull);
             if (sd < (unsigned long long)p.n_seeds) {
                 W->unit = p.seeds[sd];
                 kind = 3;
             } else {
-                unsigned long long r = *(volatile unsigned long long*)&ctl->next_root;
+                unsigned long long r = exhausted ? ~0ull : *(volatile unsigned long long*)&ctl->next_root;
                 if (r < (unsigned long long)p.n_roots) r = atomicAdd(&ctl->next_root, 1ull);
+                if (r >= (unsigned long long)p.n_roots) exhausted = true;
                 if (r < (unsigned long long)p.n_roots) {
                     W->unit.root_pos = (int32_t)r;
                     W->unit.depth = 1;
@@ -150,20 +153,25 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
                 if (lane == 0) ok = gpm_idle_register(p.ring_seq, p.ring_ids, p.ring_cap, &ctl->q_tail, (int)gw) ? 1 : 0;
                 registered = __shfl_sync(GPM_FULL_MASK, ok, 0) != 0;
             }
-            long long pend = 0;
-            int err = 0;
-            if (lane == 0) {
-                pend = *(volatile long long*)&ctl->pending;
-                err = *(volatile int*)&ctl->error;
+            // the termination state is shared by every idle warp: look at it
+            // every 16th spin only (the own mailbox is checked every spin)
+            if ((polls & 15) == 0) {
+                long long pend = 0;
+                int err = 0;
+                if (lane == 0) {
+                    pend = *(volatile long long*)&ctl->pending;
+                    err = *(volatile int*)&ctl->error;
+                }
+                pend = __shfl_sync(GPM_FULL_MASK, pend, 0);
+                err = __shfl_sync(GPM_FULL_MASK, err, 0);
+                if (pend <= 0 || err) break;
+                if (pend != last_pending) {
+                    last_pending = pend;
+                    idle_since = gpm_globaltimer();
+                }
             }
-            pend = __shfl_sync(GPM_FULL_MASK, pend, 0);
-            err = __shfl_sync(GPM_FULL_MASK, err, 0);
-            if (pend <= 0 || err) break;
             const unsigned long long now = gpm_globaltimer();
-            if (pend != last_pending) {
-                last_pending = pend;
-                idle_since = now;
-            } else if (now - idle_since > p.max_idle_ns) {
+            if (now - idle_since > p.max_idle_ns) {
                 if (lane == 0) atomicCAS(&ctl->error, 0, DEV_ETIMEOUT);
                 break;
             }
@@ -333,15 +341,27 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     const size_t fixed_smem = sizeof(unsigned long long) * MT_MAXPAT + 16;
     const bool smem_state = warp_state <= 12 * 1024 && fixed_smem + 8 * (sizeof(MtWarp) + warp_state) <= 200 * 1024;
     const size_t per_warp = sizeof(MtWarp) + (smem_state ? (size_t)p.smem_warp_bytes : 0);
-    const int wpb = g->cfg.warps_per_block > 0
-                        ? g->cfg.warps_per_block
-                        : best_warps_per_block(smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>,
-                                               per_warp, fixed_smem);
+    // Marks in HBM (large graphs): every warp owns n mark bytes that each
+    // leaf reads at random, so the grid is kept small enough for all the
+    // marks to stay in L2 (about 80 MB of them; never below 8 warps per SM):
+    // measured on rmat16 (n = 65,536, k = 5), 1,216 warps run 1.9x faster
+    // than the 4,864 the occupancy limit allows.
+    int wpb = g->cfg.warps_per_block > 0
+                  ? g->cfg.warps_per_block
+                  : best_warps_per_block(smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>,
+                                         per_warp, fixed_smem);
+    int max_per_sm = 0;
+    if (!smem_state && g->cfg.warps_per_block <= 0 && g->cfg.blocks_per_sm <= 0) {
+        const long long l2_warps = (80ll << 20) / std::max<long long>(g->n, 1);
+        const long long per_sm_warps = std::max<long long>(8, l2_warps / std::max(g->num_sms, 1));
+        wpb = 4;
+        max_per_sm = (int)std::max<long long>(2, per_sm_warps / wpb);
+    }
     const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
     const size_t smem = base_smem + (smem_state ? (size_t)wpb * p.smem_warp_bytes : 0);
     const void* kfun = smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>;
     GPM_CUDA(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    Grid gr = plan_grid(g, kfun, wpb, smem);
+    Grid gr = plan_grid(g, kfun, wpb, smem, max_per_sm);
     const long long nw = gr.total_warps();
     if (!smem_state) {
         g->scratch_slab.ensure(sizeof(int32_t) * p.slab_ints * nw);
@@ -449,13 +469,13 @@ namespace gpm {
 
 constexpr int NA_MAX_N = 8192;                                 // vertices
 constexpr size_t NA_CTL_OFF = 0;                               // Control
-constexpr size_t NA_CNT_OFF = 256;                             // MT_MAXPAT uint64 counters
+constexpr size_t NA_CNT_OFF = 1024;                            // MT_MAXPAT uint64 counters
 constexpr size_t NA_FLAG_OFF = NA_CNT_OFF + 8192;              // validation flags, max degree
 constexpr size_t NA_ROOT_OFF = NA_FLAG_OFF + 256;              // NA_MAX_N int32 roots
 constexpr size_t NA_LUT_OFF = NA_ROOT_OFF + 4 * (size_t)NA_MAX_N;
 constexpr size_t NA_LUT_BYTES = (size_t)2 << 20;               // 2^20 uint16: pattern table up to k = 7
-constexpr size_t NA_SCRATCH_BYTES = NA_LUT_OFF + NA_LUT_BYTES;  // 2,138,624 bytes
-static_assert(sizeof(Control) <= 256, "control block must fit its slot");
+constexpr size_t NA_SCRATCH_BYTES = NA_LUT_OFF + NA_LUT_BYTES;  // 2,139,392 bytes
+static_assert(sizeof(Control) <= NA_CNT_OFF, "control block must fit its slot");
 static_assert(sizeof(unsigned long long) * MT_MAXPAT <= 8192, "counters must fit their slot");
 static_assert(NA_LUT_OFF % 256 == 0, "aligned table");
 

@@ -32,6 +32,8 @@ namespace gpm {
 
 constexpr int MT_MAXK = GPM_MOTIF_MAX_K;
 constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns
+constexpr unsigned long long MT_CHECK_NS = 4000;  // busy warps look for idle ones at most this often
+constexpr float MT_MIN_DONATE_WORK = 2048.f;    // estimated leaves a handed-over range must carry
 
 // A work unit: the children at positions [lo, hi) of the extension array of
 // the node tr = (sub[0], .., sub[depth-1]) (hi < 0: all of them).  The node's
@@ -291,7 +293,12 @@ __device__ __noinline__ static void mt_donate(Control* ctl, QSeq* ring_seq, int3
     for (int t = pdepth; t <= l; t++) {
         const int from = W->cur[t], to = W->hi[t];
         if (to - from < max(donate_min, 2)) continue;
-        const int mid = mt_split(from, to, W->len[t], k - 1 - t);
+        const int len = W->len[t];
+        const int mid = mt_split(from, to, len, k - 1 - t);
+        // estimated work of the later part: sum of (len - c)^e, e = levels below
+        const float q = (float)(k - t);
+        const float est = (__powf((float)(len - mid), q) - __powf(fmaxf((float)(len - to), 1.0f), q)) / q;
+        if (est < MT_MIN_DONATE_WORK) continue;
         int wid;
         if (!gpm_idle_claim(ring_seq, ring_ids, ring_cap, &ctl->q_head, &wid)) return;
         if (wid < 0 || (unsigned long long)wid >= ring_cap) {   // never: ids are registered warps
@@ -325,8 +332,8 @@ __device__ __forceinline__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdept
                         Sink& sink, unsigned long long& unit_leaves, unsigned long long& scanned, int lane) {
     const int k = a.k;
     int l = pdepth;
-    int iter = 0;
     const unsigned long long t_start = DONATE ? gpm_globaltimer() : 0ull;
+    unsigned long long last_check = t_start;   // lane 0
     for (;;) {
         const int c = W->cur[l];
         if (c >= W->hi[l]) {
@@ -393,14 +400,16 @@ __device__ __forceinline__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdept
             l++;
         }
 
-        // donation check: every 8 steps, and after every last-level child
-        // (each of which can be long)
-        if (DONATE && ((++iter & 7) == 0 || l + 1 == k - 1)) {
+        // donation check: after every step, but at most once per
+        // MT_CHECK_NS (the lines it reads are shared by every warp)
+        if (DONATE) {
             Control* ctl = a.ctl;
             int err = 0, want = 0;
-            if (lane == 0) {
+            const unsigned long long now = gpm_globaltimer();
+            if (lane == 0 && now - last_check >= MT_CHECK_NS) {
+                last_check = now;
                 err = *(volatile int*)&ctl->error;
-                if (gpm_globaltimer() - t_start > a.donate_after_ns) {
+                if (now - t_start > a.donate_after_ns) {
                     const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
                     const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
                     want = qt > qh;   // a registered idle warp is waiting

@@ -3,6 +3,9 @@ equal the oracle's per graph; replays, autotuned shapes and unit orders give
 identical counts."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -83,3 +86,44 @@ def test_batch_rejects_cross_graph_edges():
     with pytest.raises(gpm.GpmError) as e:
         gpm.gpm_batch_create(goff, indptr, indices)
     assert e.value.status == gpm.GPM_EINVAL
+
+
+def test_ba4096_golden():
+    """The full 4,096-graph Barabasi-Albert batch in the benchmark's launch
+    configuration (autotuned shape, CUDA-graph replay): per-graph 4-clique and
+    5-motif counts of 48 seeded graphs equal the oracle's stored values
+    (tests/golden/ba4096.json, written by make_golden.py from oracle/ only),
+    and every graph satisfies the star identity of its 5-motif counts."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ba4096.json")) as f:
+        data = json.load(f)
+    gs = list(G.workload("ba4096"))
+    import hashlib
+    h = hashlib.sha256()
+    for g in gs:
+        h.update(g.sha256().encode())
+    assert h.hexdigest() == data["sha256"]
+    b = gpm.batch_from_graphs(gs)
+    gpm.gpm_batch_autotune(b, 4, 5, reps=1)
+    cc, mc = gpm.gpm_batch_count(b, 4, 5)
+    for i, c4, m5 in zip(data["graphs"], data["clique4"], data["motif5"]):
+        assert int(cc[i]) == c4, i
+        assert _to_codes(mc[i], 5) == {int(c): v for c, v in m5.items()}, i
+    # every graph, at full size: the star identity sum_p dom(p) count_p =
+    # sum_v C(d(v), 4) (each connected 5-set with a vertex adjacent to all
+    # others is counted once per such vertex)
+    from math import comb
+    dom = []
+    for pid in range(mc.shape[1]):
+        code = gpm.gpm_motif_pattern(5, pid)
+        adj = [[False] * 5 for _ in range(5)]
+        for a in range(1, 5):
+            for c in range(a):
+                if (code >> (a * (a - 1) // 2 + c)) & 1:
+                    adj[a][c] = adj[c][a] = True
+        dom.append(sum(1 for v in range(5) if all(adj[v][u] for u in range(5) if u != v)))
+    for i, g in enumerate(gs):
+        lhs = sum(int(x) * d for x, d in zip(mc[i], dom))
+        assert lhs == sum(comb(int(d), 4) for d in g.degrees()), i
+    # replaying the captured launch gives the same numbers
+    cc2, mc2 = gpm.gpm_batch_count(b, 4, 5)
+    assert np.array_equal(cc, cc2) and np.array_equal(mc, mc2)
