@@ -29,6 +29,8 @@
  *    set iff vertices j < i are adjacent.
  *  - Brute force over all k-subsets for tiny graphs (n <= 40), classifying
  *    every induced subgraph, disconnected ones included.
+ *  - Instrumentation of the clique search tree (nodes per clique size and
+ *    the bytes a sorted-list merge would move, B_alg).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *  - filter polarity: Algorithm 3 writes "if P then invalidate" while the
@@ -367,6 +369,105 @@ int orc_clique_count(int32_t n, const int32_t *indptr, const int32_t *indices, i
     if (nr < 0) return -1;
     total[0] = (uint64_t)sum;
     total[1] = (uint64_t)(sum >> 64);
+    return 0;
+}
+
+/* ------------------------------------ clique search-tree instrumentation */
+
+/*
+ * The search tree of the degree-oriented clique enumeration, measured: a node
+ * is a clique S whose candidates C(S) are the common out-neighbours of S
+ * (orientation: u -> v iff (d(u), u) < (d(v), v)).  Expanding a child v of S
+ * intersects two sorted lists, C(S) and N+(v); as a sorted-list merge reads
+ * both, that step moves 4 (|C(S)| + d+(v)) bytes.  B_alg is that sum over
+ * every child of every node of size 1 .. k-2 (the children of (k-2)-cliques
+ * give the (k-1)-cliques whose candidate counts are the k-cliques: the
+ * counted last level).  nodes[s] counts the s-cliques reached, s = 1 .. k.
+ * The paper gauges the extension step by the global load transactions it
+ * issues (its profiling table); B_alg is the analogous byte count of a
+ * sorted-list enumerator, the yardstick the GPU path's memory traffic is
+ * compared with.
+ */
+typedef struct {
+    const graph_t *g;
+    int k;
+    const int32_t *off;       /* oriented out-lists, id order */
+    const int32_t *out;
+    int32_t *cand[ORC_MAXK + 1];
+    u128 nodes[ORC_MAXK + 1];
+    u128 bytes;
+} instr_ctx;
+
+static void instr_node(instr_ctx *c, int s, const int32_t *C, int64_t nc) {
+    if (s == c->k - 1) {                 /* children are the k-cliques: counted, not expanded */
+        c->nodes[c->k] += (u128)nc;
+        return;
+    }
+    int32_t *next = c->cand[s + 1];
+    for (int64_t i = 0; i < nc; i++) {
+        int32_t v = C[i];
+        const int32_t *nv = c->out + c->off[v];
+        int64_t dv = c->off[v + 1] - c->off[v];
+        c->bytes += (u128)4 * (u128)(nc + dv);
+        int64_t a = 0, b = 0, m = 0;    /* merge of two id-sorted lists */
+        while (a < nc && b < dv) {
+            if (C[a] < nv[b]) a++;
+            else if (C[a] > nv[b]) b++;
+            else { next[m++] = C[a]; a++; b++; }
+        }
+        c->nodes[s + 1] += 1;
+        instr_node(c, s + 1, next, m);
+    }
+}
+
+/*
+ * nodes_out[2*s], nodes_out[2*s+1] = (lo, hi) of the number of s-cliques
+ * rooted at the listed roots (all vertices when roots == NULL; a clique's root
+ * is its first vertex in the orientation), s = 1 .. k; bytes_out[0..1] = (lo,
+ * hi) of B_alg.  Returns 0, -1 on bad input, -2 on allocation failure.
+ */
+int orc_clique_instrument(int32_t n, const int32_t *indptr, const int32_t *indices, int k,
+                          const int32_t *roots, int64_t n_roots, uint64_t *nodes_out, uint64_t *bytes_out) {
+    if (n < 0 || k < 1 || k > ORC_MAXK || !nodes_out || !bytes_out) return -1;
+    graph_t g = {n, indptr, indices};
+    int32_t *off = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *out = (int32_t *)malloc(sizeof(int32_t) * ((size_t)(n ? indptr[n] : 0) + 1));
+    if (!off || !out) { free(off); free(out); return -2; }
+    int32_t maxd = 0;
+    off[0] = 0;
+    for (int32_t v = 0; v < n; v++) {
+        int32_t dv = deg(&g, v), m = 0;
+        for (int32_t p = indptr[v]; p < indptr[v + 1]; p++) {
+            int32_t x = indices[p], dx = deg(&g, x);
+            if (dv < dx || (dv == dx && v < x)) out[off[v] + m++] = x;
+        }
+        off[v + 1] = off[v] + m;
+        if (m > maxd) maxd = m;
+    }
+    instr_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.g = &g; c.k = k; c.off = off; c.out = out;
+    int ok = 1;
+    for (int i = 0; i <= k; i++) {
+        c.cand[i] = (int32_t *)malloc(sizeof(int32_t) * ((size_t)maxd + 1));
+        if (!c.cand[i]) ok = 0;
+    }
+    int64_t nr = roots ? n_roots : n;
+    for (int64_t r = 0; ok && r < nr; r++) {
+        int32_t v = roots ? roots[r] : (int32_t)r;
+        if (v < 0 || v >= n) { ok = -1; break; }
+        c.nodes[1] += 1;
+        if (k >= 2) instr_node(&c, 1, out + off[v], off[v + 1] - off[v]);
+    }
+    for (int i = 0; i <= k; i++) free(c.cand[i]);
+    free(off); free(out);
+    if (ok != 1) return ok == 0 ? -2 : -1;
+    for (int s = 0; s <= k; s++) {
+        nodes_out[2 * s] = (uint64_t)c.nodes[s];
+        nodes_out[2 * s + 1] = (uint64_t)(c.nodes[s] >> 64);
+    }
+    bytes_out[0] = (uint64_t)c.bytes;
+    bytes_out[1] = (uint64_t)(c.bytes >> 64);
     return 0;
 }
 

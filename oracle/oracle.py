@@ -69,6 +69,9 @@ def _load():
             lib.orc_code_connected.restype = ctypes.c_int
             lib.orc_classes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _u64p, _i64p]
             lib.orc_classes.restype = ctypes.c_int
+            lib.orc_clique_instrument.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int, _i32p,
+                                                  ctypes.c_int64, _u64p, _u64p]
+            lib.orc_clique_instrument.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -115,6 +118,25 @@ def clique_count(g, k: int, order: int = ORDER_ID, roots=None, per_root: bool = 
     if per_root:
         return total, pr[: (nr if roots is not None else g.n)]
     return total
+
+
+def clique_instrument(g, k: int, roots=None) -> dict:
+    """Search tree of the degree-oriented clique enumeration to depth k:
+    ``nodes[s]`` = s-cliques reached (s = 1 .. k; index 0 unused) and
+    ``b_alg`` = bytes a sorted-list merge moves over every expansion of a
+    node of size <= k-2 (4 (|C(S)| + d+(v)) per child v).  With ``roots``,
+    only cliques whose first vertex in the orientation is listed."""
+    lib = _load()
+    ip, ix = _csr(g)
+    r, nr, rp = _roots(roots)
+    nodes = np.zeros(2 * (k + 1), dtype=np.uint64)
+    b = np.zeros(2, dtype=np.uint64)
+    rc = lib.orc_clique_instrument(g.n, _ptr(ip, _i32p), _ptr(ix, _i32p), k, rp, nr,
+                                   _ptr(nodes, _u64p), _ptr(b, _u64p))
+    if rc != 0:
+        raise ValueError(f"orc_clique_instrument failed ({rc})")
+    return {"nodes": [int(nodes[2 * s]) | (int(nodes[2 * s + 1]) << 64) for s in range(k + 1)],
+            "b_alg": int(b[0]) | (int(b[1]) << 64)}
 
 
 def motif_count(g, k: int, roots=None, per_root: bool = False):

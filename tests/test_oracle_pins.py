@@ -343,3 +343,77 @@ def test_motif_per_root_sums():
         for c, v in b.items():
             merged[c] = merged.get(c, 0) + v
         assert merged == full
+
+
+# ----------------------------------------- clique search-tree instrumentation
+
+def _rank_key(g):
+    d = g.degrees()
+    return lambda v: (int(d[v]), int(v))
+
+
+def _balg_bruteforce(g, k):
+    """B_alg from its definition, with sets: for every clique S of size
+    1..k-2, C(S) = vertices after all of S in the (degree, id) order and
+    adjacent to all of S; each v in C(S) adds 4 (|C(S)| + d+(v))."""
+    import networkx as nx
+    key = _rank_key(g)
+    adj = [set(g.indices[g.indptr[v]:g.indptr[v + 1]].tolist()) for v in range(g.n)]
+    dplus = [sum(1 for x in adj[v] if key(x) > key(v)) for v in range(g.n)]
+    nxg = nx.Graph()
+    nxg.add_nodes_from(range(g.n))
+    nxg.add_edges_from(g.edges().tolist())
+    total = 0
+    for S in nx.enumerate_all_cliques(nxg):
+        if len(S) > k - 2:
+            break
+        top = max(key(v) for v in S)
+        C = [v for v in range(g.n) if key(v) > top and all(v in adj[u] for u in S)]
+        total += sum(4 * (len(C) + dplus[v]) for v in C)
+    return total
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_clique_instrument_nodes_and_bytes(seed):
+    """Nodes per size equal networkx's clique counts, and B_alg equals its
+    set-based definition (a dropped level, a wrong candidate set or a wrong
+    out-degree changes one of them)."""
+    import networkx as nx
+    rng = np.random.default_rng(70 + seed)
+    g = G.gnp(int(rng.integers(8, 36)), float(rng.uniform(0.15, 0.6)), 300 + seed)
+    k = 5
+    r = O.clique_instrument(g, k)
+    nxg = nx.Graph()
+    nxg.add_nodes_from(range(g.n))
+    nxg.add_edges_from(g.edges().tolist())
+    by_size = [0] * (k + 1)
+    for S in nx.enumerate_all_cliques(nxg):
+        if len(S) > k:
+            break
+        by_size[len(S)] += 1
+    assert r["nodes"][1:] == by_size[1:]
+    assert r["b_alg"] == _balg_bruteforce(g, k)
+
+
+def test_clique_instrument_complete_graph_closed_form():
+    """K_n: nodes[s] = C(n, s); a node of size s whose last vertex has rank m
+    (C(m, s-1) of them) has n-1-m candidates, and child v (rank > m) has
+    d+(v) = n-1-v, so B_alg = sum_s sum_m C(m, s-1) sum_{v>m} 4 (2n-2-m-v)."""
+    n, k = 14, 6
+    r = O.clique_instrument(G.complete(n), k)
+    assert r["nodes"][1:] == [comb(n, s) for s in range(1, k + 1)]
+    want = sum(comb(m, s - 1) * sum(4 * ((n - 1 - m) + (n - 1 - v)) for v in range(m + 1, n))
+               for s in range(1, k - 1) for m in range(n))
+    assert r["b_alg"] == want
+
+
+def test_clique_instrument_root_partition():
+    """Per-root restriction: the roots split the tree (every clique has one
+    first vertex), so node counts and bytes add up over a root partition."""
+    g = G.gnp(40, 0.35, 9)
+    whole = O.clique_instrument(g, 5)
+    roots = np.arange(g.n, dtype=np.int32)
+    a = O.clique_instrument(g, 5, roots=roots[::2])
+    b = O.clique_instrument(g, 5, roots=roots[1::2])
+    assert [x + y for x, y in zip(a["nodes"], b["nodes"])] == whole["nodes"]
+    assert a["b_alg"] + b["b_alg"] == whole["b_alg"]
