@@ -153,8 +153,11 @@ gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, i
  * work is split and ordered (Section 4.3.5 replaced by in-kernel donation).
  */
 typedef struct {
-    int32_t warps_per_block;   /* 1, 2, 4, 8 or 16 (0 = the most resident warps/SM)    */
-    int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum)       */
+    int32_t warps_per_block;   /* 1, 2, 4, 8 or 16 (0 = automatic: the most resident   */
+                               /* warps per SM for cliques; 4 for motifs, whose grid, */
+                               /* when the marks live in HBM, is sized so that every  */
+                               /* warp's marks fit in L2)                              */
+    int32_t blocks_per_sm;     /* resident blocks per SM (0 = automatic)               */
     int32_t donate_min;        /* split a level only if >= this many siblings remain  */
     int32_t order;             /* GPM_ORDER_* root order of the plain scheduler         */
     int32_t max_idle_ms;       /* bounded wait: an idle warp gives up after this long  */
@@ -178,8 +181,8 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg);
 typedef struct {
     double   kernel_ms;        /* enumeration kernel time (CUDA events)          */
     uint64_t units_done;       /* work units (roots + donated units) finished     */
-    uint64_t donations;        /* units pushed to the donation queue              */
-    uint64_t idle_polls;       /* times an idle warp polled the queue             */
+    uint64_t donations;        /* units handed to idle warps (work donation)      */
+    uint64_t idle_polls;       /* spins of idle warps waiting for a hand-off      */
     int32_t  grid_blocks;      /* persistent grid size                            */
     int32_t  warps_per_block;
     uint64_t word_ops;         /* clique: 32-bit candidate-word AND+POPC operations; */
