@@ -331,6 +331,31 @@ def test_rmat16_full_size_identities():
     assert lhs == sum(comb(int(x), 3) for x in d)
 
 
+def test_chunglu_all_roots_per_root_matches_golden():
+    """The benchmark's launch shape -- every root of chunglu1m in one launch,
+    heaviest oriented out-degree first, donation on -- with per-root output:
+    the counts of the 320 sampled roots equal the oracle's stored per-root
+    values, and the per-root counts add up to the range call's totals."""
+    data = _golden("chunglu1m")
+    g = G.workload("chunglu1m")
+    dg = gpm.graph_from_csr(g)
+    d = g.degrees()
+    e = g.edges()
+    du, dv = d[e[:, 0]], d[e[:, 1]]
+    fwd = (du < dv) | ((du == dv) & (e[:, 0] < e[:, 1]))
+    outdeg = np.bincount(np.where(fwd, e[:, 0], e[:, 1]), minlength=g.n)
+    order = np.argsort(-outdeg, kind="stable").astype(np.int32)
+    pos = np.empty(g.n, dtype=np.int64)
+    pos[order] = np.arange(g.n)
+    totals = [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 6)]
+    for k in (4, 5, 6):
+        case = next(c for c in data["cases"] if c["app"] == "clique" and c["k"] == k)
+        c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, k, order, per_root=True)
+        assert int(c[0]) == totals[k - 4]
+        assert sum(int(x) for x in pr) == totals[k - 4]
+        assert [int(pr[pos[r]]) for r in case["roots"]] == case["per_root"], k
+
+
 def test_chunglu_range_equals_single_counts():
     """Chung-Lu n = 1,000,000, the benchmark's launch: one DFS to depth 5
     gives the same 4- and 5-clique counts as two separate calls, and the
