@@ -107,6 +107,18 @@ def profiled_traffic(summary: str, src_hash: str, units_now: float):
     return t if u > 0 and abs(units_now - u) <= 1e-6 * u else None
 
 
+def oracle_full_size(k_lo: int, k_hi: int):
+    """Full-size clique counts of chunglu1m and the list-merge bytes of the
+    depth-6 search, computed by the oracle over every root and stored by
+    tests/golden/make_golden.py (None when absent or not covering k_hi)."""
+    path = os.path.join(ROOT, "tests", "golden", "chunglu1m_full.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    return d if k_hi <= d["k_max"] else None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
 
@@ -449,6 +461,20 @@ def main():
     hbm_line = {"achieved_gbs": traffic / kern_s / 1e9 if traffic else None, "peak_gbs": hbm,
                 "frac": traffic / kern_s / 1e9 / hbm if traffic else None,
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": traffic}
+    # parity at full size against the oracle's stored totals, and the bytes a
+    # sorted-list merge enumerator would move for the same search (B_alg),
+    # expressed against the measured HBM bandwidth
+    full = oracle_full_size(args.k_lo, args.k_hi)
+    parity = None
+    list_merge = None
+    if full is not None and world == 1 and full["sha256"] == g.sha256():
+        parity = {"oracle_full_size": all(int(c) == full["cliques"][str(k)] for k, c in zip(kk, counts)),
+                  "source": "tests/golden/chunglu1m_full.json (oracle over every root)"}
+        if args.k_hi == full["k_max"]:
+            b = float(full["b_alg_depth6"])
+            list_merge = {"b_alg_bytes_per_step": b, "gbs": b / (t_step / 1000.0) / 1e9,
+                          "x_measured_hbm_peak": b / (t_step / 1000.0) / 1e9 / hbm,
+                          "definition": "sum over node expansions of 4 (|C(S)| + d+(v)) bytes (sorted-list merge)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -459,7 +485,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_ip.nbytes + h_ix.nbytes),
                 "d2h_bytes_per_step": 8 * len(kk), "ms_per_step": statistics.mean(e2e_ms)},
         "clocks": clocks, "gpu_launches": launches,
-        "roofline": roofline, "hbm": hbm_line,
+        "roofline": roofline, "hbm": hbm_line, "parity": parity, "list_merge_equivalent": list_merge,
         "sm_idle": {"idle_warp_frac": statistics.mean(idle_frac),
                     "definition": "1 - (sum over the grid's warps of time inside work units) / "
                                   "(warps x kernel time), %globaltimer"},

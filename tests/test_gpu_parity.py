@@ -331,6 +331,21 @@ def test_rmat16_full_size_identities():
     assert lhs == sum(comb(int(x), 3) for x in d)
 
 
+def test_chunglu_full_counts_match_oracle():
+    """The benchmark's workload and call at full size: one enumeration to
+    depth 6 over every root of chunglu1m (gpm_clique_count_range) gives the
+    4-, 5- and 6-clique totals the oracle computed over every root
+    (tests/golden/chunglu1m_full.json, written by make_golden.py)."""
+    with open(os.path.join(GOLDEN, "chunglu1m_full.json")) as f:
+        data = json.load(f)
+    g = G.workload("chunglu1m")
+    assert g.sha256() == data["sha256"]
+    dg = gpm.graph_from_csr(g)
+    got = [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 6)]
+    assert got == [data["cliques"][str(k)] for k in (4, 5, 6)]
+    assert gpm.gpm_clique_count(dg, 3) == data["cliques"]["3"]
+
+
 def test_chunglu_all_roots_per_root_matches_golden():
     """The benchmark's launch shape -- every root of chunglu1m in one launch,
     heaviest oriented out-degree first, donation on -- with per-root output:
