@@ -594,6 +594,144 @@ int orc_motif_count(int32_t n, const int32_t *indptr, const int32_t *indices, in
     return rc;
 }
 
+/* ------------------------------------------------ motif counting by ESU */
+
+/*
+ * The same counts by Wernicke's ESU (exclusive-neighbourhood subgraph
+ * enumeration), the reading of the canonicality filter that the GPU path
+ * follows (Section 4.4 leaves the filter to "a standard canonical filtering
+ * algorithm").  From root v the extension set is {u in N(v) : u > v};
+ * moving w from the extension set into the subgraph adds the neighbours u of
+ * w with u > v that are neither in the subgraph nor adjacent to it.  Every
+ * connected k-set is reached exactly once, from its smallest vertex.  Each
+ * set is classified as in aggregate_pattern (memoised canonical code of the
+ * induced graph).  Written for the full-size checks the Arabesque route above
+ * is too slow for; the two are compared with each other and with brute force.
+ */
+typedef struct {
+    const graph_t *g;
+    int k;
+    int32_t root;
+    int32_t sub[ORC_MAXK];
+    uint64_t code[ORC_MAXK + 1];   /* full code of sub[0..len-1] */
+    int32_t *ext[ORC_MAXK + 1];    /* extension set of depth len */
+    uint16_t *adj;                 /* per vertex: bit j = adjacent to sub[j]; bit 15 = in sub */
+    u128 *raw;                     /* k <= 7: count per full code, classified at the end */
+    canon_t canon;
+    hist_t hist;
+    u128 count;
+    int err;
+} esu_ctx;
+
+static void esu_classify(esu_ctx *c, uint64_t code) {
+    c->count += 1;
+    if (c->raw) { c->raw[code] += 1; return; }
+    uint64_t rep = canon_get(&c->canon, code);
+    if (hist_add(&c->hist, rep, 1) != 0) c->err = 1;
+}
+
+/* enter w as sub[pos] (on) or take it out (off): its own flag and its
+ * neighbours' adjacency bit pos */
+static void esu_mark(esu_ctx *c, int32_t w, int pos, int on) {
+    const graph_t *g = c->g;
+    const uint16_t bit = (uint16_t)(1u << pos);
+    if (on) {
+        c->adj[w] |= 0x8000;
+        for (int32_t p = g->indptr[w]; p < g->indptr[w + 1]; p++) c->adj[g->indices[p]] |= bit;
+    } else {
+        c->adj[w] &= 0x7fff;
+        for (int32_t p = g->indptr[w]; p < g->indptr[w + 1]; p++) c->adj[g->indices[p]] &= (uint16_t)~bit;
+    }
+}
+
+/* subgraph sub[0..len-1]; extension set ext[len][0..n) */
+static void esu_extend(esu_ctx *c, int len, int64_t n) {
+    const graph_t *g = c->g;
+    int32_t *ext = c->ext[len];
+    while (n > 0) {
+        int32_t w = ext[--n];
+        /* w's edges to sub[0..len-1] are bits 0..len-1 of its adjacency mask */
+        const uint64_t code = c->code[len] | ((uint64_t)(c->adj[w] & ((1u << len) - 1)) << pair_bit(0, len));
+        if (len + 1 == c->k) { esu_classify(c, code); continue; }
+        /* extension of sub + w: the rest of ext, then w's exclusive neighbours */
+        int32_t *nx = c->ext[len + 1];
+        int64_t m = 0;
+        for (int64_t i = 0; i < n; i++) nx[m++] = ext[i];
+        for (int32_t p = g->indptr[w]; p < g->indptr[w + 1]; p++) {
+            int32_t u = g->indices[p];
+            if (u > c->root && c->adj[u] == 0) nx[m++] = u;   /* not in sub, not adjacent to it */
+        }
+        c->sub[len] = w;
+        c->code[len + 1] = code;
+        esu_mark(c, w, len, 1);
+        esu_extend(c, len + 1, m);
+        esu_mark(c, w, len, 0);
+    }
+}
+
+/* Same interface and results as orc_motif_count. */
+int orc_motif_count_esu(int32_t n, const int32_t *indptr, const int32_t *indices, int k,
+                        const int32_t *roots, int64_t n_roots, int64_t cap,
+                        uint64_t *codes, uint64_t *lo, uint64_t *hi, int64_t *n_out,
+                        uint64_t *total, uint64_t *per_root) {
+    if (n < 0 || k < 1 || k > 8 || !n_out || !total) return -1;
+    graph_t g = {n, indptr, indices};
+    esu_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.g = &g; c.k = k;
+    int64_t maxd = 0;
+    for (int32_t v = 0; v < n; v++) if (deg(&g, v) > maxd) maxd = deg(&g, v);
+    int rc = 0;
+    if (canon_init(&c.canon, k) != 0 || hist_init(&c.hist) != 0) rc = -2;
+    c.adj = (uint16_t *)calloc((size_t)n + 1, sizeof(uint16_t));
+    if (!c.adj) rc = -2;
+    const uint64_t ncodes = k <= 7 ? (1ULL << C2(k)) : 0;
+    if (ncodes) {
+        c.raw = (u128 *)calloc((size_t)ncodes, sizeof(u128));
+        if (!c.raw) rc = -2;
+    }
+    for (int i = 0; i <= k && rc == 0; i++) {
+        c.ext[i] = (int32_t *)malloc(sizeof(int32_t) * (size_t)((int64_t)(i + 1) * maxd + 1));
+        if (!c.ext[i]) rc = -2;
+    }
+    int64_t nr = roots ? n_roots : n;
+    u128 sum = 0;
+    for (int64_t r = 0; r < nr && rc == 0; r++) {
+        int32_t v = roots ? roots[r] : (int32_t)r;
+        if (v < 0 || v >= n) { rc = -1; break; }
+        c.count = 0;
+        c.root = v;
+        c.sub[0] = v;
+        c.code[1] = 0;
+        if (k == 1) esu_classify(&c, 0);
+        else {
+            int64_t m = 0;
+            for (int32_t p = indptr[v]; p < indptr[v + 1]; p++)
+                if (indices[p] > v) c.ext[1][m++] = indices[p];
+            esu_mark(&c, v, 0, 1);
+            esu_extend(&c, 1, m);
+            esu_mark(&c, v, 0, 0);
+        }
+        sum += c.count;
+        if (per_root) per_root[r] = (c.count >> 64) ? ~0ULL : (uint64_t)c.count;
+    }
+    /* classify the full codes that occurred: one canonical lookup per code */
+    for (uint64_t x = 0; rc == 0 && x < ncodes; x++)
+        if (c.raw[x] && hist_add(&c.hist, canon_get(&c.canon, x), c.raw[x]) != 0) c.err = 1;
+    if (c.err) rc = -2;
+    if (rc == 0) {
+        *n_out = hist_export(&c.hist, cap, codes, lo, hi);
+        total[0] = (uint64_t)sum;
+        total[1] = (uint64_t)(sum >> 64);
+    }
+    for (int i = 0; i <= k; i++) free(c.ext[i]);
+    free(c.raw);
+    free(c.adj);
+    canon_free(&c.canon);
+    hist_free(&c.hist);
+    return rc;
+}
+
 /* --------------------------------------------------------- brute force */
 
 /*

@@ -58,6 +58,8 @@ def _load():
                                             ctypes.c_int64, ctypes.c_int64, _u64p, _u64p, _u64p,
                                             _i64p, _u64p, _u64p]
             lib.orc_motif_count.restype = ctypes.c_int
+            lib.orc_motif_count_esu.argtypes = lib.orc_motif_count.argtypes
+            lib.orc_motif_count_esu.restype = ctypes.c_int
             lib.orc_brute_force.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int, ctypes.c_int64,
                                             _u64p, _u64p, _u64p, _u8p, _i64p]
             lib.orc_brute_force.restype = ctypes.c_int
@@ -139,12 +141,15 @@ def clique_instrument(g, k: int, roots=None) -> dict:
             "b_alg": int(b[0]) | (int(b[1]) << 64)}
 
 
-def motif_count(g, k: int, roots=None, per_root: bool = False):
+def motif_count(g, k: int, roots=None, per_root: bool = False, method: str = "arabesque"):
     """Connected induced k-vertex subgraphs aggregated by canonical code:
     returns ``{canonical_code: count}`` (Python ints), plus per-root totals
     when ``per_root``.  With ``roots``, only sets whose smallest vertex is a
-    listed root."""
+    listed root.  ``method``: "arabesque" (Algorithm 4 with the Arabesque
+    canonical filter) or "esu" (ESU exclusive extension; same results,
+    faster, for full-size checks)."""
     lib = _load()
+    fn = {"arabesque": lib.orc_motif_count, "esu": lib.orc_motif_count_esu}[method]
     ip, ix = _csr(g)
     r, nr, rp = _roots(roots)
     cap = 1 << 14
@@ -156,7 +161,7 @@ def motif_count(g, k: int, roots=None, per_root: bool = False):
     pr = None
     if per_root:
         pr = np.zeros(max(nr if roots is not None else g.n, 1), dtype=np.uint64)
-    rc = lib.orc_motif_count(g.n, _ptr(ip, _i32p), _ptr(ix, _i32p), k, rp, nr, cap,
+    rc = fn(g.n, _ptr(ip, _i32p), _ptr(ix, _i32p), k, rp, nr, cap,
                              _ptr(codes, _u64p), _ptr(lo, _u64p), _ptr(hi, _u64p),
                              _ptr(nout, _i64p), _ptr(tot, _u64p),
                              _ptr(pr, _u64p) if pr is not None else None)

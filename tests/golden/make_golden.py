@@ -180,6 +180,64 @@ def write_chunglu_full(pool):
     print("chunglu1m_full", out["cliques"], out["b_alg_depth6"], flush=True)
 
 
+def rmat_bench_roots(g):
+    """The 512 seeded roots the learned-scheduling comparison uses: ids >=
+    1024 with degree <= 32 (seed 25)."""
+    d = g.degrees()
+    ok = (np.arange(g.n) >= 1024) & (d <= 32)
+    return G.sample_roots(g.n, 512, seed=25, exclude=~ok)
+
+
+def esu_job(spec):
+    """ESU-route motif counts of one slice of the roots (every 64th root of
+    the given root list, heaviest degree first, starting at `part`)."""
+    name, k, roots_kind, part = spec
+    g = G.workload(name)
+    if roots_kind == "all":
+        roots = np.argsort(-g.degrees(), kind="stable").astype(np.int32)
+    else:
+        roots = rmat_bench_roots(g)
+    mine = np.ascontiguousarray(roots[part::64]).astype(np.int32)
+    t = time.time()
+    pats, pr = O.motif_count(g, k, roots=mine, per_root=True, method="esu")
+    return spec, mine.tolist(), pats, [int(x) for x in pr], round(time.time() - t, 1)
+
+
+FULL_SPECS = {
+    "rmat16_full": [("rmat16", 4, "all"), ("rmat16", 5, "bench")],
+    "sbm2000_full": [("sbm2000", 5, "all"), ("sbm2000", 6, "all")],
+}
+
+
+def write_full(pool, fname):
+    """Motif counts over every root (or the 512-root benchmark sample) by the
+    oracle's ESU route, summed over 64 root slices."""
+    specs = [(name, k, kind, part) for name, k, kind in FULL_SPECS[fname] for part in range(64)]
+    res = pool.map(esu_job, specs, chunksize=1)
+    cases = []
+    for name, k, kind in FULL_SPECS[fname]:
+        pats, per_root = {}, {}
+        secs = 0.0
+        for spec, mine, p, pr, t in res:
+            if spec[:3] != (name, k, kind):
+                continue
+            for c, v in p.items():
+                pats[c] = pats.get(c, 0) + v
+            per_root.update(zip(mine, pr))
+            secs = max(secs, t)
+        g = G.workload(name)
+        roots = None if kind == "all" else [int(r) for r in rmat_bench_roots(g)]
+        cases.append({"app": "motif", "k": k, "roots": roots, "order": "id",
+                      "total": int(sum(pats.values())),
+                      "per_root": None if roots is None else [per_root[r] for r in roots],
+                      "patterns": {str(c): int(v) for c, v in sorted(pats.items())},
+                      "oracle_s": secs, "route": "esu"})
+    name = FULL_SPECS[fname][0][0]
+    with open(os.path.join(HERE, f"{fname}.json"), "w") as f:
+        json.dump({"workload": name, "sha256": G.workload(name).sha256(), "cases": cases}, f, indent=0)
+    print(fname, [(c["k"], c["total"], c["oracle_s"]) for c in cases], flush=True)
+
+
 def ba_graphs():
     """48 seeded graph indices of the 4,096-graph Barabasi-Albert batch."""
     rng = np.random.default_rng(40)
@@ -233,6 +291,10 @@ def main(names):
         with ctx.Pool(os.cpu_count() or 1) as pool:
             write_chunglu_full(pool)
         names = [n for n in names if n != "chunglu1m_full"]
+    for fname in [n for n in names if n in FULL_SPECS]:
+        with ctx.Pool(os.cpu_count() or 1) as pool:
+            write_full(pool, fname)
+    names = [n for n in names if n not in FULL_SPECS]
     specs = [s for n in names for s in SPECS[n]]
     if not specs:
         return
@@ -249,4 +311,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(SPECS) + ["ba4096", "chunglu1m_full"])
+    main(sys.argv[1:] or list(SPECS) + ["ba4096", "chunglu1m_full"] + list(FULL_SPECS))

@@ -270,13 +270,15 @@ def _golden(name):
         return json.load(f)
 
 
-@pytest.mark.parametrize("name", ["er516", "sbm2000", "rmat16", "chunglu1m"])
+@pytest.mark.parametrize("name", ["er516", "sbm2000", "rmat16", "chunglu1m", "rmat16_full", "sbm2000_full"])
 def test_workload_golden(name):
     """Full-size workloads, in the launch configuration the benchmark uses:
     full counts where the oracle finishes, else exact per-root counts on the
-    seeded root samples stored beside them."""
+    seeded root samples stored beside them (the *_full files: every root, or
+    the learned-scheduling comparison's 512 roots, by the oracle's ESU
+    route)."""
     data = _golden(name)
-    g = G.workload(name)
+    g = G.workload(data["workload"])
     assert g.sha256() == data["sha256"]
     dg = gpm.graph_from_csr(g)
     for case in data["cases"]:

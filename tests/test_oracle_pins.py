@@ -417,3 +417,35 @@ def test_clique_instrument_root_partition():
     b = O.clique_instrument(g, 5, roots=roots[1::2])
     assert [x + y for x, y in zip(a["nodes"], b["nodes"])] == whole["nodes"]
     assert a["b_alg"] + b["b_alg"] == whole["b_alg"]
+
+
+# ------------------------------------------------ the ESU route of the oracle
+
+@pytest.mark.parametrize("seed", range(8))
+def test_esu_route_matches_bruteforce_and_arabesque(seed):
+    """The oracle's ESU route (used for full-size stored values) against
+    brute force over every k-subset (its connected classes) and against the
+    Arabesque-filtered route, per pattern and per root."""
+    g = _random_small(seed, n=14)
+    for k in (1, 2, 3, 4, 5, 6):
+        esu = O.motif_count(g, k, method="esu")
+        bf = {code: c for code, (c, conn) in O.brute_force(g, k).items() if conn}
+        assert esu == bf, k
+    rng = np.random.default_rng(90 + seed)
+    h = G.gnp(int(rng.integers(20, 60)), float(rng.uniform(0.05, 0.3)), 400 + seed)
+    roots = np.arange(h.n, dtype=np.int32)[::3]
+    for k in (3, 4, 5):
+        a, pa = O.motif_count(h, k, roots=roots, per_root=True)
+        b, pb = O.motif_count(h, k, roots=roots, per_root=True, method="esu")
+        assert a == b and np.array_equal(pa, pb), k
+
+
+def test_esu_route_structured_graphs():
+    """Closed forms: K_n has C(n,k) sets, all cliques; the star K_{1,s} has
+    C(s, k-1) induced stars; the path P_n has n-k+1 induced paths."""
+    for k in (3, 4, 5):
+        assert O.motif_count(G.complete(9), k, method="esu") == {(1 << (k * (k - 1) // 2)) - 1: comb(9, k)}
+        star = O.motif_count(G.star(12), k, method="esu")
+        assert sum(star.values()) == comb(12, k - 1) and len(star) == 1
+        path = O.motif_count(G.path(15), k, method="esu")
+        assert sum(path.values()) == 15 - k + 1 and len(path) == 1
