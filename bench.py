@@ -107,6 +107,16 @@ def profiled_traffic(summary: str, src_hash: str, units_now: float):
     return t if u > 0 and abs(units_now - u) <= 1e-6 * u else None
 
 
+def golden(name: str):
+    """A stored oracle result under tests/golden/ (written by make_golden.py
+    from the oracle only), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
 def oracle_full_size(k_lo: int, k_hi: int):
     """Full-size clique counts of chunglu1m and the list-merge bytes of the
     depth-6 search, computed by the oracle over every root and stored by
@@ -282,6 +292,11 @@ def learned_vs_plain(stream, k: int = 5, n_roots: int = 512, epochs: int = 60, r
     res["spearman_degree"] = float(spearmanr(g.degrees()[roots], meas).statistic)
     res["k"] = k
     res["roots"] = f"{len(roots)} seeded roots of rmat16 (id >= 1024, degree <= 32)"
+    gd = golden("rmat16_full")
+    case = None if gd is None else next((c for c in gd["cases"] if c["k"] == k and c["roots"] is not None), None)
+    if case is not None and case["roots"] == [int(r) for r in roots]:
+        got = {str(gpm.gpm_motif_pattern(k, p)): int(x) for p, x in enumerate(ref) if x}
+        res["oracle_parity"] = got == case["patterns"] and [int(x) for x in sizes] == case["per_root"]
     res["subgraphs"] = int(ref.sum())
     res["train"] = {"samples": int(X.shape[0]), "epochs": epochs, "label_s": round(t_labels, 2),
                     "train_s": round(t_train, 2), "final_mse": model.history[-1], "first_mse": model.history[0]}
@@ -304,6 +319,12 @@ def batched_vs_plain(stream, reps: int = 5) -> dict:
         _, ms = timed(lambda: gpm.gpm_batch_count(b, 4, 5), stream)
         times.append(ms)
     total = int(cc.sum()) + int(mc.sum())
+    parity = None
+    gd = golden("ba4096")
+    if gd is not None:
+        parity = all(int(cc[i]) == c4 and {str(gpm.gpm_motif_pattern(5, p)): int(x)
+                                           for p, x in enumerate(mc[i]) if x} == m5
+                     for i, c4, m5 in zip(gd["graphs"], gd["clique4"], gd["motif5"]))
     t_b = statistics.median(times)
     idle_b = gpm.gpm_batch_get_stats(b)["idle_warp_frac"]
     # plain: every graph on its own, graphs resident on the device
@@ -319,7 +340,8 @@ def batched_vs_plain(stream, reps: int = 5) -> dict:
     b.close()
     return {"graphs": len(gs), "subgraphs": total, "batched_ms": t_b, "plain_ms": t_p,
             "batched_subgraphs_per_s": total / (t_b / 1000.0), "plain_subgraphs_per_s": total / (t_p / 1000.0),
-            "speedup": t_p / t_b, "autotuned": best, "batched_idle_warp_frac": idle_b}
+            "speedup": t_p / t_b, "autotuned": best, "batched_idle_warp_frac": idle_b,
+            "oracle_parity_48_graphs": parity}
 
 
 def main():
