@@ -599,8 +599,8 @@ int orc_motif_count(int32_t n, const int32_t *indptr, const int32_t *indices, in
 /*
  * The same counts by Wernicke's ESU (exclusive-neighbourhood subgraph
  * enumeration), the reading of the canonicality filter that the GPU path
- * follows (Section 4.4 leaves the filter to "a standard canonical filtering
- * algorithm").  From root v the extension set is {u in N(v) : u > v};
+ * follows (Section 4.4 leaves the choice of filter to a standard method).
+ * From root v the extension set is {u in N(v) : u > v};
  * moving w from the extension set into the subgraph adds the neighbours u of
  * w with u > v that are neither in the subgraph nor adjacent to it.  Every
  * connected k-set is reached exactly once, from its smallest vertex.  Each
