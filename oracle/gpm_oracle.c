@@ -471,6 +471,150 @@ int orc_clique_instrument(int32_t n, const int32_t *indptr, const int32_t *indic
     return 0;
 }
 
+/* ------------------------------- clique counting on neighbourhood bitsets */
+
+/*
+ * A third clique route, for full-size stored values that the list routes
+ * above cannot finish: the same degree-oriented search, with each node's
+ * candidate set held as a bitset over the root's out-neighbourhood instead
+ * of a sorted list.  For a root r with out-neighbours u_0 < .. < u_{d-1}
+ * (ids ascending), bit j of row i is set iff j > i and u_i, u_j are
+ * adjacent; the s-cliques whose lowest vertex (in the orientation) is r are
+ * r plus an (s-1)-clique of G[N+(r)], each reached once along increasing
+ * local indices.  A node of size s with candidates C has popc(C) children,
+ * all (s+1)-cliques; the child through i has candidates C & row_i.  Nothing
+ * here orders N+(r) by degree or trims rows: rows are full width.
+ */
+typedef struct {
+    int k;
+    int w;                    /* 64-bit words per row */
+    uint64_t *rows;           /* d x w */
+    uint64_t *cand;           /* (k + 1) x w scratch, one set per size */
+    u128 nodes[ORC_MAXK + 1]; /* s-cliques of the current root */
+} bits_ctx;
+
+static int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+static void bits_node(bits_ctx *c, int s, const uint64_t *C) {
+    u128 nc = 0;
+    for (int q = 0; q < c->w; q++) nc += (u128)popc64(C[q]);
+    c->nodes[s + 1] += nc;                   /* every candidate is an (s+1)-clique */
+    if (s + 1 >= c->k || nc == 0) return;
+    uint64_t *next = c->cand + (size_t)(s + 1) * c->w;
+    if (s + 2 == c->k) {
+        /* the children are (k-1)-cliques: add their candidate counts (the
+         * k-cliques) without descending */
+        u128 leaves = 0;
+        for (int q = 0; q < c->w; q++) {
+            uint64_t word = C[q];
+            while (word) {
+                int i = 64 * q + __builtin_ctzll(word);
+                word &= word - 1;
+                const uint64_t *row = c->rows + (size_t)i * c->w;
+                for (int z = 0; z < c->w; z++) leaves += (u128)popc64(C[z] & row[z]);
+            }
+        }
+        c->nodes[s + 2] += leaves;
+        return;
+    }
+    for (int q = 0; q < c->w; q++) {
+        uint64_t word = C[q];
+        while (word) {
+            int i = 64 * q + __builtin_ctzll(word);
+            word &= word - 1;
+            const uint64_t *row = c->rows + (size_t)i * c->w;
+            for (int z = 0; z < c->w; z++) next[z] = C[z] & row[z];
+            bits_node(c, s + 1, next);
+        }
+    }
+}
+
+/*
+ * counts_out[2*s], counts_out[2*s+1] = (lo, hi) of the number of s-cliques
+ * (s = 1 .. k) whose root is listed (all vertices when roots == NULL; the
+ * root of a clique is its first vertex in the (degree, id) orientation).
+ * per_root (nullable): n_roots x (k + 1) uint64, entry [r][s] = root r's
+ * s-cliques, saturated at 2^64-1.  Returns 0, -1 on bad input, -2 on
+ * allocation failure.
+ */
+int orc_clique_count_bits(int32_t n, const int32_t *indptr, const int32_t *indices, int k,
+                          const int32_t *roots, int64_t n_roots, uint64_t *counts_out, uint64_t *per_root) {
+    if (n < 0 || k < 1 || k > ORC_MAXK || !counts_out) return -1;
+    graph_t g = {n, indptr, indices};
+    int32_t *off = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *out = (int32_t *)malloc(sizeof(int32_t) * ((size_t)(n ? indptr[n] : 0) + 1));
+    int32_t *local = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!off || !out || !local) { free(off); free(out); free(local); return -2; }
+    int32_t maxd = 0;
+    off[0] = 0;
+    for (int32_t v = 0; v < n; v++) {
+        int32_t dv = deg(&g, v), m = 0;
+        for (int32_t p = indptr[v]; p < indptr[v + 1]; p++) {
+            int32_t x = indices[p], dx = deg(&g, x);
+            if (dv < dx || (dv == dx && v < x)) out[off[v] + m++] = x;
+        }
+        off[v + 1] = off[v] + m;
+        if (m > maxd) maxd = m;
+        local[v] = -1;
+    }
+    bits_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.k = k;
+    int wmax = (maxd + 63) / 64;
+    if (wmax < 1) wmax = 1;
+    c.rows = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)maxd + 1) * wmax);
+    c.cand = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)k + 2) * wmax);
+    int ok = (c.rows && c.cand) ? 1 : 0;
+    u128 total[ORC_MAXK + 1];
+    memset(total, 0, sizeof(total));
+    int64_t nr = roots ? n_roots : n;
+    for (int64_t t = 0; ok == 1 && t < nr; t++) {
+        int32_t r = roots ? roots[t] : (int32_t)t;
+        if (r < 0 || r >= n) { ok = -1; break; }
+        const int32_t *nb = out + off[r];
+        int32_t d = off[r + 1] - off[r];
+        int w = (d + 63) / 64;
+        if (w < 1) w = 1;
+        c.w = w;
+        memset(c.nodes, 0, sizeof(c.nodes));
+        c.nodes[1] = 1;
+        for (int32_t i = 0; i < d; i++) local[nb[i]] = i;
+        memset(c.rows, 0, sizeof(uint64_t) * (size_t)d * w);
+        /* every edge inside N+(r) is an out-edge of exactly one endpoint */
+        for (int32_t i = 0; i < d; i++) {
+            int32_t u = nb[i];
+            for (int32_t p = off[u]; p < off[u + 1]; p++) {
+                int32_t j = local[out[p]];
+                if (j < 0) continue;
+                int32_t a = i < j ? i : j, b = i < j ? j : i;
+                c.rows[(size_t)a * w + b / 64] |= 1ULL << (b % 64);
+            }
+        }
+        if (k >= 2) {
+            uint64_t *C = c.cand + (size_t)1 * w;
+            for (int q = 0; q < w; q++) {
+                int lo = 64 * q, hi = d - lo;
+                C[q] = hi >= 64 ? ~0ULL : (hi <= 0 ? 0ULL : ((1ULL << hi) - 1));
+            }
+            bits_node(&c, 1, C);
+        }
+        for (int32_t i = 0; i < d; i++) local[nb[i]] = -1;
+        for (int s = 1; s <= k; s++) {
+            total[s] += c.nodes[s];
+            if (per_root)
+                per_root[(size_t)t * (k + 1) + s] = (c.nodes[s] >> 64) ? ~0ULL : (uint64_t)c.nodes[s];
+        }
+        if (per_root) per_root[(size_t)t * (k + 1)] = 0;
+    }
+    free(c.rows); free(c.cand); free(off); free(out); free(local);
+    if (ok != 1) return ok == 0 ? -2 : -1;
+    for (int s = 0; s <= k; s++) {
+        counts_out[2 * s] = (uint64_t)total[s];
+        counts_out[2 * s + 1] = (uint64_t)(total[s] >> 64);
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------- motif counting */
 
 typedef struct {

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -41,7 +42,10 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC])
+    # -mpopcnt on x86-64 only speeds up the bitset route (hardware population
+    # count); the results are the same on every machine
+    extra = ["-mpopcnt"] if platform.machine() in ("x86_64", "AMD64") else []
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared"] + extra + ["-o", tmp, _SRC])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -74,6 +78,9 @@ def _load():
             lib.orc_clique_instrument.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int, _i32p,
                                                   ctypes.c_int64, _u64p, _u64p]
             lib.orc_clique_instrument.restype = ctypes.c_int
+            lib.orc_clique_count_bits.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int, _i32p,
+                                                  ctypes.c_int64, _u64p, _u64p]
+            lib.orc_clique_count_bits.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -139,6 +146,30 @@ def clique_instrument(g, k: int, roots=None) -> dict:
         raise ValueError(f"orc_clique_instrument failed ({rc})")
     return {"nodes": [int(nodes[2 * s]) | (int(nodes[2 * s + 1]) << 64) for s in range(k + 1)],
             "b_alg": int(b[0]) | (int(b[1]) << 64)}
+
+
+def clique_count_bits(g, k: int, roots=None, per_root: bool = False):
+    """Clique counts of every size s = 1 .. k in one degree-oriented search
+    whose candidate sets are bitsets over the root's out-neighbourhood:
+    returns ``counts`` (list, index s; index 0 unused), plus with
+    ``per_root`` a uint64 array [roots, k + 1] of each root's s-cliques.
+    With ``roots``, only cliques whose first vertex in the orientation is
+    listed (all vertices when None)."""
+    lib = _load()
+    ip, ix = _csr(g)
+    r, nr, rp = _roots(roots)
+    tot = np.zeros(2 * (k + 1), dtype=np.uint64)
+    pr = None
+    if per_root:
+        pr = np.zeros((max(nr if roots is not None else g.n, 1), k + 1), dtype=np.uint64)
+    rc = lib.orc_clique_count_bits(g.n, _ptr(ip, _i32p), _ptr(ix, _i32p), k, rp, nr, _ptr(tot, _u64p),
+                                   _ptr(pr, _u64p) if pr is not None else None)
+    if rc != 0:
+        raise ValueError(f"orc_clique_count_bits failed ({rc})")
+    counts = [int(tot[2 * s]) | (int(tot[2 * s + 1]) << 64) for s in range(k + 1)]
+    if per_root:
+        return counts, pr[: (nr if roots is not None else g.n)]
+    return counts
 
 
 def motif_count(g, k: int, roots=None, per_root: bool = False, method: str = "arabesque"):

@@ -180,6 +180,70 @@ def write_chunglu_full(pool):
     print("chunglu1m_full", out["cliques"], out["b_alg_depth6"], flush=True)
 
 
+def chunglu_heaviest_first(g):
+    """Roots of chunglu1m, heaviest oriented out-degree first (stable)."""
+    return np.argsort(-_dag_outdeg(g), kind="stable").astype(np.int32)
+
+
+def chunglu_k78_job(spec):
+    """Bitset-route clique counts of one root slice: (k, slice of the
+    heaviest-first order).  k = 7 slices are every 64th root starting at c;
+    k = 8 slices cut the 1/64 sample (every 64th root from 0) 32 ways."""
+    k, part = spec
+    g = G.workload("chunglu1m")
+    order = chunglu_heaviest_first(g)
+    roots = order[part::64] if k == 7 else order[0::64][part::32]
+    roots = np.ascontiguousarray(roots)
+    t = time.time()
+    counts, pr = O.clique_count_bits(g, k, roots=roots, per_root=True)
+    return spec, roots, counts, pr, round(time.time() - t, 1)
+
+
+def write_chunglu_k78(pool):
+    """chunglu1m clique counts at k = 7 over every root (totals per size and
+    a hash of the per-root 6- and 7-clique counts, indexed by vertex id) and
+    at k = 8 over the seeded 1/64 sample of the heaviest-first order (every
+    64th root from the heaviest; per-root 7- and 8-clique counts), by the
+    oracle's bitset route."""
+    import hashlib
+    specs = [(8, j) for j in range(32)] + [(7, c) for c in range(64)]
+    res = pool.map(chunglu_k78_job, specs, chunksize=1)
+    g = G.workload("chunglu1m")
+    tot7 = [0] * 8
+    pr7 = np.zeros((g.n, 8), dtype=np.uint64)
+    samp = {}
+    tot8 = [0] * 9
+    secs = {7: 0.0, 8: 0.0}
+    for (k, part), roots, counts, pr, t in res:
+        secs[k] = max(secs[k], t)
+        if k == 7:
+            for s in range(8):
+                tot7[s] += counts[s]
+            pr7[roots] = pr
+        else:
+            for s in range(9):
+                tot8[s] += counts[s]
+            for r, row in zip(roots.tolist(), pr):
+                samp[r] = (int(row[7]), int(row[8]))
+    order = chunglu_heaviest_first(g)
+    sample = order[0::64]
+    out = {"workload": "chunglu1m", "sha256": g.sha256(), "route": "bits",
+           "k7_all_roots": {"cliques": {str(s): int(tot7[s]) for s in range(1, 8)},
+                            "per_root_sha256": {str(s): hashlib.sha256(np.ascontiguousarray(pr7[:, s], dtype="<u8")
+                                                                       .tobytes()).hexdigest() for s in (6, 7)},
+                            "oracle_s_max_slice": secs[7]},
+           "k8_sample": {"rule": "every 64th root of the heaviest-first order (stable sort by oriented "
+                                 "out-degree, descending), starting at the heaviest",
+                         "n_roots": int(sample.shape[0]),
+                         "cliques": {str(s): int(tot8[s]) for s in range(1, 9)},
+                         "per_root": [[int(r), samp[int(r)][0], samp[int(r)][1]] for r in sample
+                                      if samp[int(r)][0]],
+                         "oracle_s_max_slice": secs[8]}}
+    with open(os.path.join(HERE, "chunglu1m_k78.json"), "w") as f:
+        json.dump(out, f, indent=0)
+    print("chunglu1m_k78", out["k7_all_roots"]["cliques"], out["k8_sample"]["cliques"], secs, flush=True)
+
+
 def rmat_bench_roots(g):
     """The 512 seeded roots the learned-scheduling comparison uses: ids >=
     1024 with degree <= 32 (seed 25)."""
@@ -287,6 +351,10 @@ def main(names):
         with ctx.Pool(os.cpu_count() or 1) as pool:
             write_ba(pool)
         names = [n for n in names if n != "ba4096"]
+    if "chunglu1m_k78" in names:
+        with ctx.Pool(max(1, (os.cpu_count() or 1) - 1)) as pool:
+            write_chunglu_k78(pool)
+        names = [n for n in names if n != "chunglu1m_k78"]
     if "chunglu1m_full" in names:
         with ctx.Pool(os.cpu_count() or 1) as pool:
             write_chunglu_full(pool)
@@ -311,4 +379,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(SPECS) + ["ba4096", "chunglu1m_full"] + list(FULL_SPECS))
+    main(sys.argv[1:] or list(SPECS) + ["ba4096", "chunglu1m_full", "chunglu1m_k78"] + list(FULL_SPECS))

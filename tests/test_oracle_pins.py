@@ -449,3 +449,67 @@ def test_esu_route_structured_graphs():
         assert sum(star.values()) == comb(12, k - 1) and len(star) == 1
         path = O.motif_count(G.path(15), k, method="esu")
         assert sum(path.values()) == 15 - k + 1 and len(path) == 1
+
+
+# ------------------------------------------------ the bitset route of the oracle
+
+def test_bits_route_complete_graph_closed_form():
+    """K_n with out-neighbourhoods wider than one 64-bit word: C(n, s)."""
+    for n in (1, 2, 9, 70, 131):
+        c = O.clique_count_bits(G.complete(n), 5)
+        assert c[1:] == [comb(n, s) for s in range(1, 6)]
+
+
+@pytest.mark.parametrize("n,r", [(17, 4), (150, 10), (12, 12), (9, 2)])
+def test_bits_route_turan(n, r):
+    g = G.turan(n, r)
+    parts = [len(range(i, n, r)) for i in range(r)]
+    k = min(r + 1, 7)
+    c = O.clique_count_bits(g, k)
+    assert c[1:] == [_elem_sym(parts, s) for s in range(1, k + 1)]
+
+
+def test_bits_route_empty_and_union():
+    g = G.disjoint_union(G.complete(6), G.complete(70), G.path(4), G.empty(3))
+    c = O.clique_count_bits(g, 6)
+    assert c[1] == g.n and c[2] == g.m
+    for s in range(3, 7):
+        assert c[s] == comb(6, s) + comb(70, s)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bits_route_vs_networkx_per_root(seed):
+    """Per size and per root (root = first vertex in the (degree, id)
+    order): networkx's cliques, counted by their lowest-ranked vertex."""
+    nx = pytest.importorskip("networkx")
+    g = _random_small(seed, n=34, p=0.5)
+    d = g.degrees()
+    h = nx.Graph()
+    h.add_nodes_from(range(g.n))
+    h.add_edges_from(map(tuple, g.edges()))
+    k = 7
+    want = np.zeros((g.n, k + 1), dtype=np.int64)
+    for c in nx.enumerate_all_cliques(h):
+        if len(c) <= k:
+            want[min(c, key=lambda v: (d[v], v)), len(c)] += 1
+    counts, pr = O.clique_count_bits(g, k, per_root=True)
+    assert counts[1:] == [int(x) for x in want.sum(axis=0)[1:]]
+    assert np.array_equal(pr[:, 1:].astype(np.int64), want[:, 1:])
+    roots = np.arange(1, g.n, 3, dtype=np.int32)
+    counts_s, pr_s = O.clique_count_bits(g, k, roots=roots, per_root=True)
+    assert counts_s[1:] == [int(x) for x in want[roots].sum(axis=0)[1:]]
+    assert np.array_equal(pr_s[:, 1:].astype(np.int64), want[roots, 1:])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bits_route_vs_list_route_wide_rows(seed):
+    """Out-neighbourhoods of 60-200 vertices (rows of 1-4 words): the same
+    per-root counts as the sorted-list route of Algorithm 4 in the (degree,
+    id) order, which the closed forms and networkx pin above."""
+    g = G.gnp(260, 0.42 + 0.05 * seed, 500 + seed)
+    roots = np.arange(0, g.n, 7, dtype=np.int32)
+    counts, pr = O.clique_count_bits(g, 5, roots=roots, per_root=True)
+    for k in (3, 4, 5):
+        tot, want = O.clique_count(g, k, order=O.ORDER_DEGREE, roots=roots, per_root=True)
+        assert counts[k] == tot
+        assert np.array_equal(pr[:, k], want)
