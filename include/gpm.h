@@ -168,6 +168,9 @@ typedef struct {
     int32_t clique_compact;    /* two-level clique tail on the node's members (rows of ceil(|C|/32)   */
                                /* words instead of ceil(d/32)): 0 never, 1 when |C| >= 48 and the    */
                                /* rows get shorter, 2 whenever they get shorter                     */
+    int32_t motif_agg_min;     /* motif: a node one level above the leaves whose extension array     */
+                               /* has at least this many entries left counts its last two levels by  */
+                               /* entry class instead of leaf by leaf (0: never)                     */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */
@@ -206,13 +209,15 @@ gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
 #define GPM_MLP_PARAMS 4801   /* W1 64x8, b1 64, W2 64x64, b2 64, w3 64, b3 1 (row-major, this order) */
 
 /*
- * Per-vertex features, FP32 [n][8]: log1p of degree, of oriented out-degree,
- * of the number of higher-id neighbours, of the neighbour-degree sum, of the
- * higher-id neighbour-degree sum, of the triangles rooted at v (lowest
- * (degree, id) vertex), of the largest neighbour degree; and v / n.
+ * Per-vertex features for subgraph size k, FP32 [n][8]: log1p of degree, of
+ * oriented out-degree, of the number of higher-id neighbours, of the
+ * neighbour-degree sum (2-hop degree sum), of the higher-id neighbour-degree
+ * sum, of the triangles rooted at v (lowest (degree, id) vertex), of the core
+ * number of v (k-core decomposition); and k / 8, so that one network can
+ * predict sizes for several k.  1 <= k <= GPM_CLIQUE_MAX_K.
  * out: n*8 floats, a device pointer if flags has GPM_DEVICE_PTRS, else host.
  */
-gpm_status gpm_root_features(gpm_graph* g, float* out, uint32_t flags);
+gpm_status gpm_root_features(gpm_graph* g, int k, float* out, uint32_t flags);
 
 /*
  * y[i] = MLP(x[i]) for i < n.  w_bf16: GPM_MLP_PARAMS BF16 values (as
@@ -336,7 +341,9 @@ gpm_status gpm_batch_get_stats(const gpm_batch* b, gpm_stats* out);
  *
  * The first call on a device looks up the device address of the scratch
  * array (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  The host-side pattern table of each k is
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or any reset of the device's primary
+ * context) this entry point must not be called again in that process.  The host-side pattern table of each k is
  * built once per process in host memory.  Every call on a device shares the
  * one scratch array, which keeps the last call's contents (each call clears
  * what must start at zero): calls that overlap on the GPU -- on different

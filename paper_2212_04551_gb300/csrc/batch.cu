@@ -52,7 +52,7 @@ struct gpm_batch {
         size_t words = 0;
         int blocks = 0, wpb = 0;
     };
-    std::map<std::tuple<int, int, int, int, int>, Captured> graphs;   // (kc, km, wpb, bps, order)
+    std::map<std::tuple<int, int, int, int, int, int>, Captured> graphs;   // (kc, km, wpb, bps, order, motif_agg_min)
 };
 
 namespace gpm {
@@ -76,6 +76,7 @@ struct BatchParams {
     int mark_stride;
     long long lvl_off[MT_MAXK + 1];
     int slab_ints;
+    int agg_min, agg_words;               // aggregated motif tail (mt_tail_agg)
     int warp_bytes;
     unsigned long long* clique_out;       // [G]
     unsigned long long* motif_out;        // [G][npat]
@@ -120,7 +121,8 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     unsigned char* mt = base + (size_t)p.cq_words * 4;
     MtWarp* W = reinterpret_cast<MtWarp*>(mt);
     unsigned long long* wc = reinterpret_cast<unsigned long long*>(mt + ((sizeof(MtWarp) + 15) & ~size_t(15)));
-    unsigned char* marks = reinterpret_cast<unsigned char*>(wc + ((p.npat + 1) & ~1));
+    uint32_t* agg = reinterpret_cast<uint32_t*>(wc + ((p.npat + 1) & ~1));
+    unsigned char* marks = reinterpret_cast<unsigned char*>(agg + ((p.agg_words + 3) & ~3));
     int32_t* slab = reinterpret_cast<int32_t*>(marks + p.mark_stride);
     MotifWalk mw;
     mw.indptr = p.indptr;
@@ -140,6 +142,8 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     mw.donate_min = 0;
     mw.donate_after_ns = 0;
     mw.err = &p.ctl->error;
+    mw.agg = p.agg_words > 0 ? agg : nullptr;
+    mw.agg_min = p.agg_words > 0 ? p.agg_min : 0;
     for (int v = lane; v < p.mark_stride; v += 32) marks[v] = 0;
     for (int j = lane; j < p.npat; j += 32) wc[j] = 0ull;
     __syncwarp();
@@ -253,7 +257,7 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     gpm_graph* g = b->g;
     const int wpb = b->cfg.warps_per_block > 0 ? b->cfg.warps_per_block : 8;
     const int bps = b->cfg.blocks_per_sm;
-    const auto key = std::make_tuple(kc, km, wpb, bps, b->order_mode);
+    const auto key = std::make_tuple(kc, km, wpb, bps, b->order_mode, b->cfg.motif_agg_min);
     auto it = b->graphs.find(key);
     if (it != b->graphs.end()) return it->second;
 
@@ -290,8 +294,10 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
         off = (off + 3) & ~3ll;
     }
     p.slab_ints = (int)std::max(off, 4ll);
+    p.agg_min = b->cfg.motif_agg_min;
+    p.agg_words = (km > 0 && p.agg_min > 0) ? mt_agg_words(km) : 0;
     const size_t mt_bytes = ((sizeof(MtWarp) + 15) & ~size_t(15)) + sizeof(unsigned long long) * ((npat + 1) & ~1) +
-                            p.mark_stride + 4 * (size_t)p.slab_ints;
+                            4 * (size_t)((p.agg_words + 3) & ~3) + p.mark_stride + 4 * (size_t)p.slab_ints;
     p.warp_bytes = (int)((p.cq_words * 4 + mt_bytes + 15) & ~size_t(15));
     const size_t smem = (size_t)wpb * p.warp_bytes;
     if (smem > 227 * 1024) fail(GPM_ENOTIMPL, "batched state does not fit in shared memory (graphs too large)");

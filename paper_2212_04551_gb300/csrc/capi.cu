@@ -225,6 +225,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.donate_after_us < 0) fail(GPM_EINVAL, "donate_after_us < 0");
         if (c.clique_tail != 0 && c.clique_tail != 2 && c.clique_tail != 3) fail(GPM_EINVAL, "clique_tail must be 0, 2 or 3");
         if (c.clique_compact < 0 || c.clique_compact > 2) fail(GPM_EINVAL, "clique_compact must be 0, 1 or 2");
+        if (c.motif_agg_min < 0) fail(GPM_EINVAL, "motif_agg_min < 0");
         g->cfg = c;
     });
 }
@@ -237,16 +238,17 @@ gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out) {
     });
 }
 
-gpm_status gpm_root_features(gpm_graph* g, float* out, uint32_t flags) {
+gpm_status gpm_root_features(gpm_graph* g, int k, float* out, uint32_t flags) {
     return guarded([&] {
         check_graph(g);
         if (!out) fail(GPM_EINVAL, "out is NULL");
+        if (k < 1 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "k out of range [1, 16]");
         if (flags & GPM_DEVICE_PTRS) {
-            root_features(g, out);
+            root_features(g, k, out);
         } else {
             DevBuf tmp;
             tmp.ensure(sizeof(float) * 8 * std::max(g->n, 1));
-            root_features(g, tmp.as<float>());
+            root_features(g, k, tmp.as<float>());
             GPM_CUDA(cudaMemcpyAsync(out, tmp.ptr, sizeof(float) * 8 * g->n, cudaMemcpyDeviceToHost, g->stream));
             GPM_CUDA(cudaStreamSynchronize(g->stream));
         }

@@ -163,6 +163,9 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         if (kind == 2) registered = false;
 
         if (!kind) {
+            // without donation nothing can arrive once the roots and seeds
+            // are gone: leave instead of waiting for the others to finish
+            if (!p.donate) break;
             // ---- idle: register once for a hand-off, then wait (bounded) on
             // this warp's own mailbox or global completion
             if (!idle) {

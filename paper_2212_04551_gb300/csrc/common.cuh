@@ -187,7 +187,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
                int split_chunks = 0);
 
 // sched.cu
-void root_features(gpm_graph* g, float* d_out);
+void root_features(gpm_graph* g, int k, float* d_out);
 void mlp_forward(const uint16_t* w, const float* x, int64_t n, float* y, cudaStream_t s);
 void mlp_grad(const uint16_t* w, const float* x, const float* t, int64_t n, float* grad, float* loss, cudaStream_t s);
 void mlp_adam(float* master, float* m, float* v, const float* grad, int step, float lr, uint16_t* w, cudaStream_t s);

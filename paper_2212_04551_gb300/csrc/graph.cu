@@ -381,6 +381,7 @@ gpm_config default_config() {
     c.donate_after_us = 50;
     c.clique_tail = 0;
     c.clique_compact = 0;
+    c.motif_agg_min = 16;
     return c;
 }
 

@@ -49,6 +49,8 @@ struct MotifParams {
     unsigned long long donate_after_ns;
     unsigned long long max_idle_ns;
     unsigned long long* counts; // npat global counters
+    int agg_min;                // aggregated last two levels from this many entries (0: never)
+    int agg_words;              // shared words of class counters per warp (mt_agg_words(k))
 };
 
 template <bool SMEM_STATE>
@@ -59,6 +61,8 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     const int nwb = blockDim.x >> 5;
     unsigned long long* bcnt = reinterpret_cast<unsigned long long*>(smem_raw);
     MtWarp* W = reinterpret_cast<MtWarp*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT) + wib;
+    uint32_t* agg = reinterpret_cast<uint32_t*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb) +
+                    (size_t)wib * p.agg_words;
     for (int j = threadIdx.x; j < p.npat; j += blockDim.x) bcnt[j] = 0ull;
 
     const long long gw = (long long)blockIdx.x * nwb + wib;
@@ -79,8 +83,11 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     a.donate_min = p.donate_min;
     a.donate_after_ns = p.donate_after_ns;
     a.err = &ctl->error;
+    a.agg = p.agg_words > 0 ? agg : nullptr;
+    a.agg_min = p.agg_words > 0 ? p.agg_min : 0;
     if (SMEM_STATE) {
-        unsigned char* tail = smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb;
+        unsigned char* tail = smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb +
+                              sizeof(uint32_t) * (size_t)p.agg_words * nwb;
         tail = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tail) + 15) & ~uintptr_t(15));
         a.mk = tail + (size_t)wib * p.smem_warp_bytes;
         a.slab = reinterpret_cast<int32_t*>(a.mk + p.mark_stride);
@@ -141,6 +148,9 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         if (kind == 2) registered = false;
 
         if (!kind) {
+            // without donation nothing can arrive once the roots and seeds
+            // are gone: leave instead of waiting for the others to finish
+            if (!p.donate) break;
             // ---- idle: register once for a hand-off, then wait (bounded) on
             // this warp's own mailbox or global completion
             if (!idle) {
@@ -339,8 +349,12 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     const long long warp_state = (long long)p.mark_stride + 4 * p.slab_ints;
     p.smem_warp_bytes = (int)((warp_state + 15) & ~15ll);
     const size_t fixed_smem = sizeof(unsigned long long) * MT_MAXPAT + 16;
-    const bool smem_state = warp_state <= 12 * 1024 && fixed_smem + 8 * (sizeof(MtWarp) + warp_state) <= 200 * 1024;
-    const size_t per_warp = sizeof(MtWarp) + (smem_state ? (size_t)p.smem_warp_bytes : 0);
+    p.agg_min = g->cfg.motif_agg_min;
+    p.agg_words = p.agg_min > 0 ? mt_agg_words(k) : 0;
+    const size_t agg_bytes = sizeof(uint32_t) * (size_t)p.agg_words;
+    const bool smem_state =
+        warp_state <= 12 * 1024 && fixed_smem + 8 * (sizeof(MtWarp) + agg_bytes + warp_state) <= 200 * 1024;
+    const size_t per_warp = sizeof(MtWarp) + agg_bytes + (smem_state ? (size_t)p.smem_warp_bytes : 0);
     // Marks in HBM (large graphs): every warp owns n mark bytes that each
     // leaf reads at random, so the grid is kept small enough for all the
     // marks to stay in L2 (about 80 MB of them; never below 8 warps per SM):
@@ -361,7 +375,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
         wpb = 4;
         max_per_sm = (int)std::max<long long>(2, per_sm_warps / wpb);
     }
-    const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
+    const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + (sizeof(MtWarp) + agg_bytes) * wpb + 16;
     const size_t smem = base_smem + (smem_state ? (size_t)wpb * p.smem_warp_bytes : 0);
     const void* kfun = smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>;
     GPM_CUDA(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -587,6 +601,8 @@ static void motif_count_noalloc(const int32_t* indptr, const int32_t* indices, i
     p.mark_stride = (int)((n + 15) & ~15);
     const long long warp_state = (long long)p.mark_stride + 4 * p.slab_ints;
     const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * wpb + 16;
+    p.agg_min = 0;    // per-leaf counting only: no class counters in this launch's shared memory
+    p.agg_words = 0;
     p.smem_warp_bytes = (int)((warp_state + 15) & ~15ll);
     const size_t smem = base_smem + (size_t)wpb * p.smem_warp_bytes;
     if (warp_state > 12 * 1024 || smem > 200 * 1024)
@@ -625,6 +641,7 @@ static void motif_count_noalloc(const int32_t* indptr, const int32_t* indices, i
     GPM_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
     GPM_CUDA(cudaMemcpyAsync(host, dcounts, sizeof(unsigned long long) * npat, cudaMemcpyDeviceToHost, s));
     GPM_CUDA(cudaStreamSynchronize(s));
+    if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "a bounded device wait ran out");
     if (h.error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
     if (h.error >= DEV_ECHECK) fail(GPM_ECUDA, "device consistency check " + std::to_string(h.error - DEV_ECHECK) + " failed");
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));

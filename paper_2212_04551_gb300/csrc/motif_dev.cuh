@@ -81,7 +81,19 @@ struct MotifWalk {
     int donate_min;
     unsigned long long donate_after_ns;   // a unit splits only after running this long
     int* err;                   // device error flag
+    // aggregated last two levels (mt_tail_agg): this warp's class counters
+    // (mt_agg_words(k) words of shared memory), used when a node one level
+    // above the leaves has at least agg_min entries left (agg == nullptr or
+    // agg_min <= 0: never)
+    uint32_t* agg;
+    int agg_min;
 };
+
+// 32-bit words of one warp's class counters for size k: HA, HB, E (one per
+// class) and the adjacent-pair table P (classes x classes), classes = 2^(k-2)
+__host__ __device__ constexpr int mt_agg_words(int k) {
+    return k < 3 ? 0 : 3 * (1 << (k - 2)) + (1 << (k - 2)) * (1 << (k - 2));
+}
 
 __device__ __forceinline__ int mt_code_off(int i) { return i * (i - 1) / 2 - 1; }   // bits of v_i, i >= 2
 
@@ -324,6 +336,152 @@ __device__ __noinline__ static void mt_donate(Control* ctl, QSeq* ring_seq, int3
     }
 }
 
+// The last two levels below a node tr of size k-2 (level l = k-2, array ext
+// of length L), counted by class instead of leaf by leaf.  Its children are
+// w = ext[c], c in A = [cur, hi); child w is the (k-1)-set tr+w, and its
+// k-vertex leaves are tr+w+x for every later entry x = ext[c'] (c' > c) and
+// for every exclusive neighbour x of w (above the root, neither in tr nor
+// adjacent to it).  The induced graph of a leaf is fixed by code(tr), the
+// class of w and of x -- an entry's class is its adjacency to tr, mark bits
+// 0 .. k-3 -- and whether w and x are adjacent.  So:
+//
+//   * pairs {w, x} of entries: with HA / HB the class histograms of A and of
+//     B = [hi, L), the pairs of classes {s1, s2} number C(HA[s],2) (s1 = s2)
+//     or HA[s1] HA[s2] within A, plus HA[s1] HB[s2] (+ HA[s2] HB[s1]) across;
+//     of these, the adjacent ones are found by scanning N(w) for every w in A
+//     (an entry x of A counted from its smaller endpoint only, an entry of B
+//     always), and the rest are non-adjacent;
+//   * exclusive neighbours: counted per class of w during the same scans.
+//
+// One scan of N(w) per child replaces the per-leaf walk over the later
+// entries (quadratic in L).  Mark bits 6 and 5 flag the entries of A u B and
+// of B during the call (free at this level: tr uses bits 0 .. k-3 and 7).
+// The adjacency lists of 32 children at a time are scanned as one flattened
+// range, so every lane has an entry whatever the degrees.
+template <class Sink>
+__device__ __noinline__ void mt_tail_agg(const MotifWalk& a, MtWarp* W, int l, const int32_t* ext, int root,
+                                         Sink& sink, unsigned long long& leaves, unsigned long long& scanned,
+                                         int lane) {
+    const int C = 1 << l;                        // classes: adjacency to tr[0 .. l-1]
+    const unsigned lowtr = (unsigned)C - 1u;
+    const int a0 = W->cur[l], a1 = W->hi[l], L = W->len[l];
+    uint32_t* HA = a.agg;
+    uint32_t* HB = HA + C;
+    uint32_t* E = HB + C;
+    uint32_t* P = E + C;                         // P[s1 * C + s2], s1 <= s2
+    for (int i = lane; i < 3 * C + C * C; i += 32) HA[i] = 0u;
+    __syncwarp();
+    // classes of A and B, and their range marks
+    for (int j0 = a0; j0 < L; j0 += 32) {
+        const int j = j0 + lane;
+        int key = -1;
+        if (j < L) {
+            const int x = ext[j];
+            const unsigned char m = a.mk[x - a.mbase];
+            a.mk[x - a.mbase] = m | (unsigned char)(j < a1 ? 0x40 : 0x60);
+            key = (int)(m & lowtr) + (j < a1 ? 0 : C);
+        }
+        const unsigned grp = __match_any_sync(GPM_FULL_MASK, key);
+        if (key >= 0 && lane == __ffs(grp) - 1) HA[key] += (uint32_t)__popc(grp);
+    }
+    __syncwarp();
+    // scan N(w) for the children, 32 at a time
+    for (int c0 = a0; c0 < a1; c0 += 32) {
+        const int c = c0 + lane;
+        int w = 0, sw = 0, b = 0, e = 0;
+        if (c < a1) {
+            w = ext[c];
+            sw = a.mk[w - a.mbase] & lowtr;
+            int lo = a.indptr[w], hi = a.indptr[w + 1];
+            e = hi;
+            while (lo < hi) {                    // first neighbour above the root
+                const int mid = (lo + hi) >> 1;
+                if (a.indices[mid] <= root) lo = mid + 1; else hi = mid;
+            }
+            b = lo;
+        }
+        const int len = e - b;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(GPM_FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int pre = incl - len;
+        const int total = __shfl_sync(GPM_FULL_MASK, incl, 31);
+        if (lane == 0) scanned += (unsigned)total;
+        for (int f0 = 0; f0 < total; f0 += 32) {
+            const int f = f0 + lane;
+            int t = 0;                           // owner: the last lane with pre <= f
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int pc = __shfl_sync(GPM_FULL_MASK, pre, t + step);
+                if (pc <= f) t += step;
+            }
+            const int wt = __shfl_sync(GPM_FULL_MASK, w, t);
+            const int st = __shfl_sync(GPM_FULL_MASK, sw, t);
+            const int bt = __shfl_sync(GPM_FULL_MASK, b, t);
+            const int pt = __shfl_sync(GPM_FULL_MASK, pre, t);
+            int ke = -1, kp = -1;
+            if (f < total) {
+                const int x = a.indices[bt + (f - pt)];
+                const unsigned char m = a.mk[x - a.mbase];
+                if ((m & (lowtr | 0x80u)) == 0) {
+                    ke = st;                     // exclusive neighbour of w
+                } else if ((m & 0x40) && ((m & 0x20) || x > wt)) {
+                    const int s2 = m & lowtr;    // adjacent pair of entries
+                    kp = min(st, s2) * C + max(st, s2);
+                }
+            }
+            unsigned grp = __match_any_sync(GPM_FULL_MASK, ke);
+            if (ke >= 0 && lane == __ffs(grp) - 1) E[ke] += (uint32_t)__popc(grp);
+            grp = __match_any_sync(GPM_FULL_MASK, kp);
+            if (kp >= 0 && lane == __ffs(grp) - 1) P[kp] += (uint32_t)__popc(grp);
+        }
+    }
+    __syncwarp();
+    // patterns: w = v_l (bits at mt_code_off(l), none for l = 1), x = v_{l+1}
+    const int codetr = l >= 2 ? W->code[l] : 0;
+    const int offx = mt_code_off(l + 1);
+    unsigned long long mine = 0;
+    for (int idx = lane; idx < C * C; idx += 32) {
+        const int s1 = idx >> l, s2 = idx & (C - 1);
+        if (s1 > s2) continue;
+        const unsigned long long ha1 = HA[s1], ha2 = HA[s2], hb1 = HB[s1], hb2 = HB[s2];
+        const unsigned long long within = s1 == s2 ? ha1 * (ha1 - (ha1 ? 1 : 0)) / 2 : ha1 * ha2;
+        const unsigned long long across = ha1 * hb2 + (s1 != s2 ? ha2 * hb1 : 0ull);
+        const unsigned long long adj = P[idx];
+        const unsigned long long non = within + across - adj;
+        const int cw = codetr | (l >= 2 ? (s1 << mt_code_off(l)) : 0);
+        if (non) {
+            const int pid = a.lut[cw | (s2 << offx)];
+            if (pid == 0xffff) atomicExch(a.err, DEV_EINVAL);
+            else sink.add(pid, non);
+            mine += non;
+        }
+        if (adj) {
+            const int pid = a.lut[cw | ((s2 | C) << offx)];
+            if (pid == 0xffff) atomicExch(a.err, DEV_EINVAL);
+            else sink.add(pid, adj);
+            mine += adj;
+        }
+    }
+    for (int s1 = lane; s1 < C; s1 += 32) {
+        if (!E[s1]) continue;
+        const int cw = codetr | (l >= 2 ? (s1 << mt_code_off(l)) : 0);
+        const int pid = a.lut[cw | (C << offx)];
+        if (pid == 0xffff) atomicExch(a.err, DEV_EINVAL);
+        else sink.add(pid, (unsigned long long)E[s1]);
+        mine += E[s1];
+    }
+    leaves += mine;
+    // drop the range marks
+    for (int j = a0 + lane; j < L; j += 32) a.mk[ext[j] - a.mbase] &= (unsigned char)0x9f;
+    __syncwarp();
+    if (lane == 0) W->cur[l] = a1;
+    __syncwarp();
+}
+
 // Walk the unit whose node is at depth pdepth (W->cur/hi/len[pdepth] set,
 // unit_ext = its extension array).  Returns false if it stopped on a device
 // error (marks are then left dirty).  unit_leaves: lane-private leaf count.
@@ -351,6 +509,13 @@ __device__ __forceinline__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdept
             continue;
         }
         const int32_t* ext = l == pdepth ? unit_ext : a.slab + a.lvl_off[l];
+        if (l + 2 == k && a.agg_min > 0 && W->len[l] - c >= a.agg_min) {
+            // one level above the leaves with many entries left: count the
+            // remaining children's leaves by class (then pop)
+            __syncwarp();
+            mt_tail_agg(a, W, l, ext, root, sink, unit_leaves, scanned, lane);
+            continue;
+        }
         const int w = ext[c];
         __syncwarp();                       // every lane has read cur[l] before it moves on
         if (lane == 0) W->cur[l] = c + 1;

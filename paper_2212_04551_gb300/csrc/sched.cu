@@ -7,12 +7,12 @@
 // layer.  The network only changes which warp runs which part of the search,
 // never what is counted.
 //
-//   features (FP32, per vertex v):
+//   features (FP32, per vertex v, for subgraph size k):
 //     f0 log1p d(v)            f1 log1p d+(v) (degree-ordered out-degree)
 //     f2 log1p |{u in N(v): u > v}|       (motif root's first extension set)
 //     f3 log1p sum_{u in N(v)} d(u)       f4 log1p sum_{u in N(v), u > v} d(u)
 //     f5 log1p triangles whose lowest (degree, id) vertex is v
-//     f6 log1p max_{u in N(v)} d(u)       f7 v / n
+//     f6 log1p core number of v           f7 k / 8 (one network serves several k)
 //   network: 8 -> 64 -> 64 -> 1, ReLU, BF16 weights, FP32 activations and
 //   accumulation; trained with MSE on log-sizes and Adam on FP32 master weights.
 //
@@ -66,21 +66,62 @@ __global__ void k_tri_root(const int32_t* __restrict__ off, const int32_t* __res
     }
 }
 
+// Core numbers by peeling (the k-core decomposition): at level c every
+// remaining vertex whose remaining degree is <= c gets core number c and is
+// removed, which lowers its remaining neighbours' degrees; a level is
+// repeated until it removes nothing, then c moves to the smallest remaining
+// degree.  One pass of one level: flags[0] = 1 if it removed a vertex,
+// flags[1] = the smallest remaining degree among the vertices it kept.
+__global__ void k_core_init(const int32_t* __restrict__ deg, int32_t n, int32_t* __restrict__ rem,
+                            int32_t* __restrict__ core) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        rem[v] = deg[v];
+        core[v] = -1;
+    }
+}
+
+__global__ void k_core_peel(const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices, int32_t n,
+                            int32_t c, int32_t* __restrict__ rem, int32_t* __restrict__ core, int* __restrict__ flags) {
+    int removed = 0, keep_min = INT32_MAX;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        if (core[v] >= 0) continue;
+        const int r = atomicAdd(&rem[v], 0);
+        if (r <= c) {
+            core[v] = c;
+            removed = 1;
+            for (int t = indptr[v]; t < indptr[v + 1]; t++) {
+                const int u = indices[t];
+                if (atomicAdd(&core[u], 0) < 0) atomicSub(&rem[u], 1);
+            }
+        } else {
+            keep_min = min(keep_min, r);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        removed |= __shfl_xor_sync(GPM_FULL_MASK, removed, o);
+        keep_min = min(keep_min, __shfl_xor_sync(GPM_FULL_MASK, keep_min, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (removed) atomicOr(&flags[0], 1);
+        if (keep_min != INT32_MAX) atomicMin(&flags[1], keep_min);
+    }
+}
+
 __global__ void k_features(const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
                            const int32_t* __restrict__ deg, const int32_t* __restrict__ outdeg,
-                           const float* __restrict__ tri, int32_t n, float* __restrict__ out) {
+                           const float* __restrict__ tri, const int32_t* __restrict__ core, int32_t n, int k,
+                           float* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long v = warp; v < n; v += nw) {
         const int b = indptr[v], e = indptr[v + 1];
         double s_all = 0, s_up = 0;
-        int c_up = 0, mx = 0;
+        int c_up = 0;
         for (int t = b + lane; t < e; t += 32) {
             const int u = indices[t];
             const int du = deg[u];
             s_all += du;
-            mx = max(mx, du);
             if (u > v) {
                 s_up += du;
                 c_up++;
@@ -90,7 +131,6 @@ __global__ void k_features(const int32_t* __restrict__ indptr, const int32_t* __
             s_all += __shfl_xor_sync(GPM_FULL_MASK, s_all, o);
             s_up += __shfl_xor_sync(GPM_FULL_MASK, s_up, o);
             c_up += __shfl_xor_sync(GPM_FULL_MASK, c_up, o);
-            mx = max(mx, __shfl_xor_sync(GPM_FULL_MASK, mx, o));
         }
         if (lane == 0) {
             float* f = out + v * MLP_IN;
@@ -100,8 +140,8 @@ __global__ void k_features(const int32_t* __restrict__ indptr, const int32_t* __
             f[3] = (float)log1p(s_all);
             f[4] = (float)log1p(s_up);
             f[5] = log1pf(tri[v]);
-            f[6] = log1pf((float)mx);
-            f[7] = n > 0 ? (float)v / (float)n : 0.f;
+            f[6] = log1pf((float)core[v]);
+            f[7] = (float)k / 8.f;
         }
     }
 }
@@ -111,17 +151,46 @@ static int blocks_for(int64_t items_x32, int threads, int sms) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sms * 32));
 }
 
-void root_features(gpm_graph* g, float* d_out) {
+// core numbers of every vertex into d_core (host-driven peeling passes)
+static void core_numbers(gpm_graph* g, int32_t* d_core, DevBuf& tmp) {
+    cudaStream_t s = g->stream;
+    const int32_t n = g->n;
+    tmp.ensure(sizeof(int32_t) * ((size_t)n + 8));
+    int32_t* rem = tmp.as<int32_t>();
+    int* flags = reinterpret_cast<int*>(rem + n);
+    const int blocks = blocks_for((int64_t)n, 256, g->num_sms);
+    k_core_init<<<blocks, 256, 0, s>>>(g->degree.as<int32_t>(), n, rem, d_core);
+    GPM_CUDA(cudaGetLastError());
+    int c = 0;
+    for (long long pass = 0;; pass++) {
+        if (pass > 4ll * n + 16) fail(GPM_ECUDA, "core decomposition did not converge");
+        const int init[2] = {0, INT32_MAX};
+        GPM_CUDA(cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        k_core_peel<<<blocks, 256, 0, s>>>(g->indptr.as<int32_t>(), g->indices.as<int32_t>(), n, c, rem, d_core,
+                                           flags);
+        GPM_CUDA(cudaGetLastError());
+        int h[2];
+        GPM_CUDA(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GPM_CUDA(cudaStreamSynchronize(s));
+        if (h[0]) continue;              // level c removed something: run it again
+        if (h[1] == INT32_MAX) break;    // nothing left
+        c = std::max(c + 1, h[1]);
+    }
+}
+
+void root_features(gpm_graph* g, int k, float* d_out) {
     ensure_dag(g);
     cudaStream_t s = g->stream;
-    DevBuf tri;
+    DevBuf tri, core, tmp;
     tri.ensure(sizeof(float) * std::max(g->n, 1));
+    core.ensure(sizeof(int32_t) * std::max(g->n, 1));
     if (g->n > 0) {
+        core_numbers(g, core.as<int32_t>(), tmp);
         k_tri_root<<<blocks_for((int64_t)g->n * 32, 256, g->num_sms), 256, 0, s>>>(
             g->dag_off.as<int32_t>(), g->dag_adj.as<int32_t>(), g->dag_outdeg.as<int32_t>(), g->n, tri.as<float>());
         k_features<<<blocks_for((int64_t)g->n * 32, 256, g->num_sms), 256, 0, s>>>(
             g->indptr.as<int32_t>(), g->indices.as<int32_t>(), g->degree.as<int32_t>(), g->dag_outdeg.as<int32_t>(),
-            tri.as<float>(), g->n, d_out);
+            tri.as<float>(), core.as<int32_t>(), g->n, k, d_out);
         GPM_CUDA(cudaGetLastError());
     }
     GPM_CUDA(cudaStreamSynchronize(s));

@@ -45,7 +45,7 @@ class gpm_config(ctypes.Structure):
                 ("donate_min", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
                 ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32),
-                ("clique_compact", ctypes.c_int32)]
+                ("clique_compact", ctypes.c_int32), ("motif_agg_min", ctypes.c_int32)]
 
 
 class gpm_stats(ctypes.Structure):
@@ -79,7 +79,7 @@ SIGNATURES = {
     "gpm_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
     "gpm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
     "gpm_last_error": (ctypes.c_char_p, []),
-    "gpm_root_features": (ctypes.c_int, [_vp, _vp, ctypes.c_uint32]),
+    "gpm_root_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint32]),
     "gpm_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
     "gpm_mlp_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]),
     "gpm_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp, _vp]),
@@ -298,14 +298,14 @@ def _dev_ptr(t, what: str) -> int:
     return t.data_ptr()
 
 
-def gpm_root_features(g: Graph, out=None):
-    """Per-vertex FP32 features [n][8]; into ``out`` (CUDA tensor) or a new host array."""
+def gpm_root_features(g: Graph, k: int, out=None):
+    """Per-vertex FP32 features [n][8] for size k; into ``out`` (CUDA tensor) or a new host array."""
     n = gpm_graph_info(g)[0]
     if out is None:
         arr = np.zeros((max(n, 1), 8), dtype=np.float32)
-        _check(load().gpm_root_features(g, arr.ctypes.data, 0), "gpm_root_features")
+        _check(load().gpm_root_features(g, int(k), arr.ctypes.data, 0), "gpm_root_features")
         return arr[:n]
-    _check(load().gpm_root_features(g, _dev_ptr(out, "out"), GPM_DEVICE_PTRS), "gpm_root_features")
+    _check(load().gpm_root_features(g, int(k), _dev_ptr(out, "out"), GPM_DEVICE_PTRS), "gpm_root_features")
     return out
 
 
@@ -425,6 +425,7 @@ def gpm_batch_set_config(b: Batch, **kw) -> None:
     c.max_idle_ms = 120000
     c.donate = 1
     c.donate_after_us = 50
+    c.motif_agg_min = 16
     for key, val in kw.items():
         setattr(c, key, int(val))
     _check(load().gpm_batch_set_config(b, ctypes.byref(c)), "gpm_batch_set_config")

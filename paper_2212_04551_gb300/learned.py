@@ -67,10 +67,10 @@ def new_model(seed: int = 0, stream=None) -> Model:
     return Model(master, w, m, v)
 
 
-def features(dg, n: int):
+def features(dg, n: int, k: int):
     import torch
     x = torch.empty((max(n, 1), D_IN), dtype=torch.float32, device="cuda")
-    gpm.gpm_root_features(dg, x)
+    gpm.gpm_root_features(dg, k, x)
     return x[:n]
 
 
@@ -80,16 +80,20 @@ def root_sizes(dg, app: int, k: int) -> np.ndarray:
     return pr.astype(np.float64)
 
 
-def training_set(app: int = gpm.GPM_APP_MOTIF, k: int = 5, seeds=range(100, 132), scale: int = 12,
+def training_set(app: int = gpm.GPM_APP_MOTIF, k=5, seeds=range(100, 132), scale: int = 12,
                  edge_factor: int = 8, stream=None):
-    """(X, T) on the device: features and log1p(size) of every root of every graph."""
+    """(X, T) on the device: features and log1p(size) of every root of every
+    graph, for each size in ``k`` (an int or a sequence of ints; the size is
+    feature f7, so one network learns all of them)."""
     import torch
+    ks = [k] if isinstance(k, int) else list(k)
     xs, ts = [], []
     for seed in seeds:
         g = G.rmat(scale, edge_factor, 0.57, 0.19, 0.19, seed)
         dg = gpm.graph_from_csr(g, stream=stream)
-        xs.append(features(dg, g.n))
-        ts.append(torch.from_numpy(np.log1p(root_sizes(dg, app, k)).astype(np.float32)).cuda())
+        for kk in ks:
+            xs.append(features(dg, g.n, kk))
+            ts.append(torch.from_numpy(np.log1p(root_sizes(dg, app, kk)).astype(np.float32)).cuda())
         dg.close()
     return torch.cat(xs), torch.cat(ts)
 

@@ -61,6 +61,32 @@ def test_motif_random_graphs(seed):
         assert motif_by_code(dg, k) == O.motif_count(g, k), (seed, k)
 
 
+@pytest.mark.parametrize("agg_min", [0, 1, 16])
+def test_motif_tail_modes(agg_min):
+    """The last two motif levels counted leaf by leaf (agg_min 0) or by entry
+    class (1: every node one level above the leaves; 16: nodes with at least
+    16 entries left), on random graphs, a hub and planted blocks: the
+    oracle's per-pattern counts, per root as well."""
+    cases = [random_graph(s) for s in range(40, 52)] + [G.star(70), G.sbm(240, 40, 0.35, 0.03, 8),
+                                                        G.disjoint_union(G.complete(9), G.path(6))]
+    for g in cases:
+        dg = gpm.graph_from_csr(g)
+        gpm.gpm_set_config(dg, motif_agg_min=agg_min)
+        for k in range(3, 7):
+            if comb(g.n, k) > 3_000_000:
+                break
+            assert motif_by_code(dg, k) == O.motif_count(g, k), (g.n, k)
+    g = G.gnp(60, 0.15, 41)
+    dg = gpm.graph_from_csr(g)
+    gpm.gpm_set_config(dg, motif_agg_min=agg_min, donate_after_us=0, donate_min=2)
+    roots = np.arange(0, 60, 2, dtype=np.int32)
+    for k in (4, 5, 6, 7):
+        c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, k, roots, per_root=True)
+        want, opr = O.motif_count(g, k, roots=roots, per_root=True)
+        assert {gpm.gpm_motif_pattern(k, p): int(x) for p, x in enumerate(c) if x} == want, k
+        assert np.array_equal(pr, opr), k
+
+
 def test_motif_k7_random():
     for seed in range(4):
         g = G.gnp(40, 0.12, 900 + seed)
@@ -208,7 +234,8 @@ def _schedule_reference():
     dict(donate=0), dict(donate=1, donate_min=2, donate_after_us=0), dict(warps_per_block=4),
     dict(warps_per_block=16, blocks_per_sm=1), dict(order=gpm.GPM_ORDER_ID),
     dict(warps_per_block=1, blocks_per_sm=1), dict(clique_tail=2), dict(clique_tail=3, warps_per_block=2),
-    dict(clique_compact=1), dict(clique_compact=2)])
+    dict(clique_compact=1), dict(clique_compact=2), dict(motif_agg_min=0), dict(motif_agg_min=1),
+    dict(motif_agg_min=1, donate=1, donate_min=2, donate_after_us=0)])
 def test_schedule_never_changes_counts(cfg):
     g, ref_c, ref_m = _schedule_reference()
     dg = gpm.graph_from_csr(g)
@@ -240,21 +267,23 @@ def test_invalid_csr_rejected(bad):
 
 
 def test_bounded_wait_times_out_and_recovers():
-    """One heavy root and donation off: every other warp is idle while
-    nothing completes, so with a 1 ms idle limit the wait runs out and the
-    call returns GPM_ETIMEOUT (the busy warp sees the flag and stops); the
-    same graph then counts correctly with the default limit."""
+    """One heavy root whose warp never hands work over (donation on, but only
+    after ~35 minutes of running): every other warp registers and waits on
+    its mailbox while nothing completes, so with a 1 ms idle limit the wait
+    runs out and the call returns GPM_ETIMEOUT (the busy warp sees the flag
+    and stops); the same graph then counts correctly with the default
+    limits."""
     g = G.complete(140)
     dg = gpm.graph_from_csr(g)
     root = np.array([0], dtype=np.int32)
-    gpm.gpm_set_config(dg, donate=0, max_idle_ms=1)
+    gpm.gpm_set_config(dg, donate=1, donate_after_us=2_000_000_000, max_idle_ms=1)
     with pytest.raises(gpm.GpmError) as e:
         gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, 7, root)
     assert e.value.status == gpm.GPM_ETIMEOUT
     with pytest.raises(gpm.GpmError) as e:
-        gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, 5, root)
+        gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, 6, root)
     assert e.value.status == gpm.GPM_ETIMEOUT
-    gpm.gpm_set_config(dg, donate=1, max_idle_ms=120000)
+    gpm.gpm_set_config(dg, donate=1, donate_after_us=50, max_idle_ms=120000)
     assert gpm.gpm_clique_count(dg, 5) == comb(140, 5)
     got = gpm.gpm_motif_count(dg, 4)
     assert int(got.sum()) == comb(140, 4) and int(got[-1]) == comb(140, 4)

@@ -112,10 +112,19 @@ def test_training_reduces_loss_on_held_out_graphs(torch):
     assert M.spearman(pred, Th.cpu().numpy()) > 0.5
 
 
-def test_features_match_definition(torch):
-    g = G.gnp(60, 0.15, 4)
+@pytest.mark.parametrize("k", [4, 6])
+def test_features_match_definition(torch, k):
+    """Every feature against its definition, computed here on the host:
+    degrees and neighbour sums with numpy, triangles per root by the oracle,
+    core numbers by networkx."""
+    nx = pytest.importorskip("networkx")
+    g = G.disjoint_union(G.gnp(60, 0.15, 4), G.complete(7), G.star(9), G.path(5))
     dg = gpm.graph_from_csr(g)
-    f = gpm.gpm_root_features(dg)
+    f = gpm.gpm_root_features(dg, k)
+    h = nx.Graph()
+    h.add_nodes_from(range(g.n))
+    h.add_edges_from(map(tuple, g.edges()))
+    core = nx.core_number(h)
     d = g.degrees()
     e = g.edges()
     outdeg = np.zeros(g.n, dtype=np.int64)
@@ -129,7 +138,7 @@ def test_features_match_definition(torch):
         nb = g.indices[g.indptr[v]:g.indptr[v + 1]]
         up = nb[nb > v]
         want = [np.log1p(d[v]), np.log1p(outdeg[v]), np.log1p(len(up)), np.log1p(d[nb].sum()),
-                np.log1p(d[up].sum()), np.log1p(tri_root[v]), np.log1p(d[nb].max() if len(nb) else 0), v / g.n]
+                np.log1p(d[up].sum()), np.log1p(tri_root[v]), np.log1p(core[v]), k / 8]
         assert np.allclose(f[v], want, rtol=1e-5, atol=1e-6), v
 
 
@@ -140,7 +149,7 @@ def test_schedules_never_change_counts(torch, app):
     k = 4
     roots = G.sample_roots(g.n, 700, seed=3)
     ref, ref_pr = gpm.gpm_count_roots(dg, app, k, roots, per_root=True)
-    X = L.features(dg, g.n)
+    X = L.features(dg, g.n, k)
     model = L.new_model(1)
     pred = L.predict(model, X)
     rng = np.random.default_rng(0)
