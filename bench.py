@@ -3,19 +3,28 @@
 Default workload (the plain method at scale): k-clique counting on the
 Chung-Lu power-law graph (n = 1,000,000, average degree 16, exponent 2.1,
 expected degrees capped at 20,000, seed 1), degree-ordered, int32 CSR.  One
-step = one enumeration that counts every clique size k_lo..k_hi
+step = one enumeration that counts every clique size 4..7
 (gpm_clique_count_range), with the graph already resident in HBM.  The
-default range is 4..6 (a step of about half a second); ``--k-hi 7`` and
-``--k-hi 8`` run deeper ranges of the same configuration (seconds to hours:
-the 8-clique count is about 1e15).
+configuration's full range 4..8 is one enumeration of about three minutes:
+it is timed once, beside the steps, as the ``k4_8`` entry.
+
+Beside the headline the line carries one timed, oracle-checked entry per
+workload of the method (``configs``): 4-vertex motifs on a 516-vertex
+Erdos-Renyi graph (plain call and CUDA-graph replay), 5-vertex motifs over
+every root of an R-MAT scale-16 graph (plain vs learned scheduling, plus
+6- and 7-vertex motifs on a stratified root sample), 4,096 small
+Barabasi-Albert graphs (batched launch vs the plain kernel on their union
+vs one plain call per graph), and deep cliques plus 6-vertex motifs on a
+stochastic block model graph (plain vs learned).
 
 Printed: one JSON line (rank 0) with the metric, the device-timed value,
 the end-to-end value through the C ABI with host buffers (graph creation
 from host CSR + counting + result read-back inside the timed region), the
 roofline of the dominant kernel, SM clocks sampled during the timed region,
-and the CPU oracle timed on a bounded root sample of the same workload.
+and the CPU oracle on a stratified root sample of the same workload, run on
+every host core.
 
-``--impl reference`` times the CPU oracle alone on that bounded sample (the
+``--impl reference`` times the CPU oracle alone on such samples (the
 reference arm for this method is the plain CPU restatement of the paper's
 enumeration).
 
@@ -26,6 +35,7 @@ summed on the host; value = all subgraphs / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import os
 import statistics
@@ -33,6 +43,7 @@ import subprocess
 import sys
 import threading
 import time
+from math import comb
 
 import numpy as np
 
@@ -51,10 +62,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpm", choices=["gpm", "reference"])
     ap.add_argument("--k-lo", type=int, default=4)
-    ap.add_argument("--k-hi", type=int, default=6)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
+    ap.add_argument("--k-hi", type=int, default=7)
+    ap.add_argument("--cpu-stride", type=int, default=512,
+                    help="oracle sample: every this-many-th root of the heaviest-first order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip the learned and batched comparisons")
+    ap.add_argument("--no-k8", action="store_true", help="skip the timed k = 4..8 enumeration")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-workload entries")
     return ap.parse_args()
 
 
@@ -117,16 +130,18 @@ def golden(name: str):
         return json.load(f)
 
 
-def oracle_full_size(k_lo: int, k_hi: int):
-    """Full-size clique counts of chunglu1m and the list-merge bytes of the
-    depth-6 search, computed by the oracle over every root and stored by
-    tests/golden/make_golden.py (None when absent or not covering k_hi)."""
-    path = os.path.join(ROOT, "tests", "golden", "chunglu1m_full.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        d = json.load(f)
-    return d if k_hi <= d["k_max"] else None
+def oracle_clique_totals(g) -> dict:
+    """Full-size clique totals of chunglu1m per size, from the stored oracle
+    runs over every root (k <= 6: list route; k = 7: bitset route)."""
+    out = {}
+    for name, key in (("chunglu1m_full", None), ("chunglu1m_k78", "k7_all_roots")):
+        d = golden(name)
+        if d is None or d["sha256"] != g.sha256():
+            continue
+        src = d["cliques"] if key is None else d[key]["cliques"]
+        for s, v in src.items():
+            out[int(s)] = int(v)
+    return out
 
 
 class ClockSampler:
@@ -194,29 +209,32 @@ def dag_out_degrees(g) -> np.ndarray:
     return np.bincount(np.where(fwd, e[:, 0], e[:, 1]), minlength=g.n)
 
 
-def cpu_baseline(g, k_lo, k_hi, budget_s):
-    """The oracle, as it stands, on a bounded seeded root sample of the same
-    workload: roots drawn uniformly, counted one k at a time until the time
-    budget is spent.  Returns (subgraphs/s, description, roots used)."""
+def heaviest_first(g) -> np.ndarray:
+    return np.argsort(-dag_out_degrees(g), kind="stable").astype(np.int32)
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(g, k_lo, k_hi, stride, offset=0, cores=None):
+    """The oracle (its bitset clique route, every size k_lo..k_hi in one
+    pass) on a stratified root sample of the same workload -- every
+    ``stride``-th root of the heaviest-first order from ``offset``, so heavy
+    and light roots are mixed as in the full run -- spread over the host
+    cores by threads (the oracle's C code runs without the interpreter lock).
+    Returns (subgraphs/s, description, cores used, subgraphs, seconds)."""
     from oracle import oracle as O
-    from paper_2212_04551_gb300 import graphs as G
     O.build()
-    perm = G.sample_roots(g.n, g.n, seed=99)          # all roots, seeded order
-    rng = np.random.default_rng(99)
-    rng.shuffle(perm)
-    done = 0
-    found = 0
+    roots = heaviest_first(g)[offset::stride]
+    cores = cores or os.cpu_count() or 1
+    chunks = [np.ascontiguousarray(roots[i::cores * 4]) for i in range(cores * 4)]
     t0 = time.perf_counter()
-    chunk = 64
-    while time.perf_counter() - t0 < budget_s and done < g.n:
-        roots = perm[done:done + chunk]
-        for k in range(k_lo, k_hi + 1):
-            found += O.clique_count(g, k, order=O.ORDER_DEGREE, roots=roots)
-        done += roots.shape[0]
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        res = list(ex.map(lambda r: O.clique_count_bits(g, k_hi, roots=r), chunks))
     el = time.perf_counter() - t0
-    desc = (f"oracle clique k={k_lo}..{k_hi} (Algorithm 4, one k per pass) on {done} seeded uniform roots "
-            f"of {g.n} ({el:.1f} s, single thread)")
-    return found / el, desc, done
+    found = sum(sum(c[k] for k in range(k_lo, k_hi + 1)) for c in res)
+    desc = (f"oracle clique k={k_lo}..{k_hi} (bitset route, one pass) on every {stride}th root of the "
+            f"heaviest-first order from {offset} ({roots.shape[0]} roots, {el:.1f} s on {cores} threads)")
+    return found / el, desc, cores, found, el
 
 
 def timed(fn, stream):
@@ -230,89 +248,177 @@ def timed(fn, stream):
     return out, e0.elapsed_time(e1)
 
 
-def learned_vs_plain(stream, k: int = 5, n_roots: int = 512, epochs: int = 60, reps: int = 2) -> dict:
-    """Learned scheduling (the MLP trained on R-MAT scale-12 graphs, seeds
-    100-131, with per-root sizes measured by the plain enumerator) against the
-    plain heaviest-degree-first donation scheduler, on the R-MAT scale-16 graph
-    restricted to a seeded sample of roots (ids >= 1024, degree <= 32);
-    counts must agree exactly."""
-    import torch
+def by_code(k, counts) -> dict:
+    from paper_2212_04551_gb300 import gpm
+    return {str(gpm.gpm_motif_pattern(k, p)): int(x) for p, x in enumerate(counts) if x}
 
+
+def dominating(k, code) -> int:
+    adj = [[False] * k for _ in range(k)]
+    for i in range(1, k):
+        for j in range(i):
+            if (code >> (i * (i - 1) // 2 + j)) & 1:
+                adj[i][j] = adj[j][i] = True
+    return sum(1 for v in range(k) if all(adj[v][u] for u in range(k) if u != v))
+
+
+def motif_stats(dg) -> dict:
+    from paper_2212_04551_gb300 import gpm
+    st = gpm.gpm_get_stats(dg)
+    return {"kernel_ms": st["kernel_ms"], "donations": int(st["donations"]), "units": int(st["units_done"]),
+            "idle_warp_frac": st["idle_warp_frac"], "adjacency_entries": int(st["word_ops"]),
+            "grid": [int(st["grid_blocks"]), int(st["warps_per_block"])]}
+
+
+# ---------------------------------------------------------- learned scheduler
+
+class Learned:
+    """The subtree-size MLP and an untrained copy (the ablation).  The trained
+    network is the one shipped with the package -- trained by the library's
+    own kernels on sizes the plain enumerator measured (motif counting, k = 5
+    and 6, every root of the 32 R-MAT scale-12 graphs of seeds 100-131; its
+    record rides along) -- or, when that file is absent, one trained here on
+    the k = 5 sizes only (the k = 6 labels take minutes)."""
+
+    def __init__(self, stream, epochs=40):
+        from paper_2212_04551_gb300 import gpm
+        from paper_2212_04551_gb300 import learned as L
+        self.stream = stream
+        self.untrained = L.new_model(0, stream)
+        if os.path.exists(L.WEIGHTS):
+            self.model, rec = L.load(L.WEIGHTS, stream)
+            self.info = {"source": os.path.relpath(L.WEIGHTS, ROOT), **rec}
+            return
+        t0 = time.perf_counter()
+        X, T = L.training_set(gpm.GPM_APP_MOTIF, (5,), seeds=range(100, 132), scale=12, stream=stream)
+        label_s = time.perf_counter() - t0
+        self.model = L.new_model(0, stream)
+        t0 = time.perf_counter()
+        L.train(self.model, X, T, epochs=epochs, batch=4096, lr=3e-3, stream=stream)
+        import torch
+        torch.cuda.synchronize()
+        self.info = {"source": "trained in this run", "k": [5], "samples": int(X.shape[0]), "epochs": epochs,
+                     "label_s": round(label_s, 2), "train_s": round(time.perf_counter() - t0, 2),
+                     "first_mse": self.model.history[0], "final_mse": self.model.history[-1]}
+
+    def compare(self, dg, g, k, roots=None, reps=1, arms=("plain", "learned", "untrained"), static=False):
+        """Plain (heaviest degree first, donation) against the learned and
+        untrained schedules on the same root set; counts must agree."""
+        from scipy.stats import spearmanr
+
+        from paper_2212_04551_gb300 import gpm
+        from paper_2212_04551_gb300 import learned as L
+        feats = L.features(dg, g.n, k)
+        preds = {"learned": L.predict(self.model, feats, self.stream),
+                 "untrained": L.predict(self.untrained, feats, self.stream)}
+        n_roots = g.n if roots is None else len(roots)
+        out, ref, sizes = {}, None, None
+        for donate in ((1, 0) if static else (1,)):
+            gpm.gpm_set_config(dg, donate=donate)
+            tag = "donation" if donate else "static"
+            res = {}
+            for name in arms:
+                if name == "plain":
+                    gpm.gpm_sched_from_scores(dg, gpm.GPM_APP_MOTIF, None, roots, 0, 0)
+                    plan = {"split_roots": 0, "chunks": 0}
+                else:
+                    plan = L.schedule(dg, gpm.GPM_APP_MOTIF, preds[name], roots, warps=4864, chunks=8)
+                times = []
+                for _ in range(reps):
+                    (c, pr), ms = timed(lambda: gpm.gpm_count_scheduled(dg, gpm.GPM_APP_MOTIF, k, n_roots=n_roots,
+                                                                        per_root=True), self.stream)
+                    times.append(ms)
+                if ref is None:
+                    ref, sizes = c, pr
+                assert np.array_equal(c, ref), f"{name} schedule changed the counts"
+                ms = statistics.median(times)
+                res[name] = {"ms": ms, "subgraphs_per_s": int(ref.sum()) / (ms / 1000.0), **motif_stats(dg), **plan}
+            if "plain" in res and "learned" in res:
+                res["speedup_learned_vs_plain"] = res["plain"]["ms"] / res["learned"]["ms"]
+            if "plain" in res and "untrained" in res:
+                res["speedup_untrained_vs_plain"] = res["plain"]["ms"] / res["untrained"]["ms"]
+            out[tag] = res
+        gpm.gpm_set_config(dg, donate=1)
+        sel = np.arange(g.n) if roots is None else np.asarray(roots)
+        meas = np.log1p(sizes.astype(np.float64))
+        out["spearman_trained"] = float(spearmanr(preds["learned"].cpu().numpy()[sel], meas).statistic)
+        out["spearman_untrained"] = float(spearmanr(preds["untrained"].cpu().numpy()[sel], meas).statistic)
+        out["spearman_degree"] = float(spearmanr(g.degrees()[sel], meas).statistic)
+        return out, ref, sizes
+
+
+# ------------------------------------------------------------ per-workload
+
+def config_er516(stream) -> dict:
+    """4-vertex motifs of the 516-vertex Erdos-Renyi graph: the plain call
+    (median of 20) and one persistent launch captured in a CUDA graph,
+    replayed 100 times (time / 100)."""
     from paper_2212_04551_gb300 import gpm
     from paper_2212_04551_gb300 import graphs as G
-    from paper_2212_04551_gb300 import learned as L
-    t0 = time.perf_counter()
-    X, T = L.training_set(gpm.GPM_APP_MOTIF, k, seeds=range(100, 132), scale=12, stream=stream)
-    t_labels = time.perf_counter() - t0
-    model = L.new_model(0, stream)
-    untrained = L.new_model(0, stream)
-    t0 = time.perf_counter()
-    L.train(model, X, T, epochs=epochs, batch=4096, lr=3e-3, stream=stream)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    g = G.workload("rmat16")
-    d = g.degrees()
-    ok = (np.arange(g.n) >= 1024) & (d <= 32)
-    roots = G.sample_roots(g.n, n_roots, seed=25, exclude=~ok)
+    g = G.workload("er516")
     dg = gpm.graph_from_csr(g, stream=stream)
-    feats = L.features(dg, g.n)
-    pred_trained = L.predict(model, feats, stream)
-    pred_untrained = L.predict(untrained, feats, stream)
-    res = {}
-    ref = None
-    sizes = None
-    for donate in (1, 0):
-        gpm.gpm_set_config(dg, donate=donate)
-        tag = "donation" if donate else "static"
-        res[tag] = {}
-        for name, pred in (("plain", None), ("learned", pred_trained), ("untrained", pred_untrained)):
-            if pred is None:
-                gpm.gpm_sched_from_scores(dg, gpm.GPM_APP_MOTIF, None, roots, 0, 0)
-                plan = {"split_roots": 0, "chunks": 0}
-            else:
-                plan = L.schedule(dg, gpm.GPM_APP_MOTIF, pred, roots, warps=4864, chunks=8)
-            times = []
-            for _ in range(reps):
-                (c, pr), ms = timed(lambda: gpm.gpm_count_scheduled(dg, gpm.GPM_APP_MOTIF, k, n_roots=len(roots),
-                                                                    per_root=True), stream)
-                times.append(ms)
-            st = gpm.gpm_get_stats(dg)
-            if ref is None:
-                ref, sizes = c, pr
-            assert np.array_equal(c, ref), f"{name} schedule changed the counts"
-            ms = statistics.median(times)
-            res[tag][name] = {"ms": ms, "subgraphs_per_s": int(ref.sum()) / (ms / 1000.0),
-                              "donations": int(st["donations"]), "units": int(st["units_done"]),
-                              "idle_warp_frac": st["idle_warp_frac"], **plan}
-        res[tag]["speedup_learned_vs_plain"] = res[tag]["plain"]["ms"] / res[tag]["learned"]["ms"]
-    from scipy.stats import spearmanr
-    meas = np.log1p(sizes.astype(np.float64))
-    res["spearman_trained"] = float(spearmanr(pred_trained.cpu().numpy()[roots], meas).statistic)
-    res["spearman_untrained"] = float(spearmanr(pred_untrained.cpu().numpy()[roots], meas).statistic)
-    res["spearman_degree"] = float(spearmanr(g.degrees()[roots], meas).statistic)
-    res["k"] = k
-    res["roots"] = f"{len(roots)} seeded roots of rmat16 (id >= 1024, degree <= 32)"
-    gd = golden("rmat16_full")
-    case = None if gd is None else next((c for c in gd["cases"] if c["k"] == k and c["roots"] is not None), None)
-    if case is not None and case["roots"] == [int(r) for r in roots]:
-        got = {str(gpm.gpm_motif_pattern(k, p)): int(x) for p, x in enumerate(ref) if x}
-        res["oracle_parity"] = got == case["patterns"] and [int(x) for x in sizes] == case["per_root"]
-    res["subgraphs"] = int(ref.sum())
-    res["train"] = {"samples": int(X.shape[0]), "epochs": epochs, "label_s": round(t_labels, 2),
-                    "train_s": round(t_train, 2), "final_mse": model.history[-1], "first_mse": model.history[0]}
+    c = gpm.gpm_motif_count(dg, 4)
+    kms, wall = [], []
+    for _ in range(20):
+        t0 = time.perf_counter()
+        gpm.gpm_motif_count(dg, 4)
+        wall.append((time.perf_counter() - t0) * 1000)
+        kms.append(gpm.gpm_get_stats(dg)["kernel_ms"])
+    b = gpm.batch_from_graphs([g], stream=stream)
+    _, bm = gpm.gpm_batch_count(b, 0, 4)
+    _, ms100 = timed(lambda: [gpm.gpm_batch_count(b, 0, 4) for _ in range(100)], stream)
+    gd = golden("er516")
+    want = next(cs["patterns"] for cs in gd["cases"] if cs["app"] == "motif" and cs["k"] == 4) if gd else None
+    total = int(c.sum())
+    b.close()
+    dg.close()
+    return {"workload": "er516 motif k=4 (n=516, m=1,200, seed 0)", "subgraphs": total,
+            "plain_kernel_ms": statistics.median(kms), "plain_call_ms": statistics.median(wall),
+            "plain_subgraphs_per_s": total / (statistics.median(wall) / 1000.0),
+            "graph_replay_ms": ms100 / 100.0, "graph_replay_subgraphs_per_s": total / (ms100 / 100.0 / 1000.0),
+            "oracle_parity": (by_code(4, c) == want and by_code(4, bm[0]) == want) if want else None}
+
+
+def config_rmat16(stream, learned: Learned) -> dict:
+    """5-vertex motifs over every root of R-MAT scale 16 (hub of degree 6,444
+    at id 0), plain and learned; pinned by the star identity
+    sum_p dom(p) count_p = sum_v C(d(v), 4).  6- and 7-vertex motifs on the
+    stratified root samples stored beside the oracle's counts."""
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    g = G.workload("rmat16")
+    dg = gpm.graph_from_csr(g, stream=stream)
+    d = g.degrees()
+    res = {"workload": "rmat16 motif k=5 every root (R-MAT scale 16, edge factor 8, seed 2)"}
+    cmp5, c5, _ = learned.compare(dg, g, 5, None, reps=1, arms=("plain", "learned"))
+    lhs = sum(dominating(5, gpm.gpm_motif_pattern(5, p)) * int(x) for p, x in enumerate(c5))
+    res["k5_all_roots"] = {"subgraphs": int(c5.sum()), **cmp5,
+                           "star_identity": lhs == sum(comb(int(x), 4) for x in d)}
+    gs = golden("rmat16_strat")
+    if gs is not None and gs["sha256"] == g.sha256():
+        for case in gs["cases"]:
+            k, roots = case["k"], np.array(case["roots"], dtype=np.int32)
+            cmp, c, pr = learned.compare(dg, g, k, roots, reps=1, static=False)
+            res[f"k{k}_sample"] = {"roots": len(roots), "sample": case["rule"], "subgraphs": int(c.sum()), **cmp,
+                                   "oracle_parity": by_code(k, c) == case["patterns"]
+                                   and [int(x) for x in pr] == case["per_root"]}
     dg.close()
     return res
 
 
-def batched_vs_plain(stream, reps: int = 5) -> dict:
+def config_ba4096(stream, reps: int = 5) -> dict:
     """4,096 Barabasi-Albert graphs, per-graph 4-clique and 5-motif counts:
-    one autotuned, CUDA-graph-captured persistent launch against the plain
-    form (one gpm_clique_count + one gpm_motif_count per graph)."""
+    one autotuned, CUDA-graph-captured persistent launch, against the plain
+    kernel on the same graphs packed as one disjoint union (one clique call
+    + one motif call: the same subgraphs, but no per-graph results), and
+    against one plain call per graph (warmed, median of 3 passes)."""
     from paper_2212_04551_gb300 import gpm
     from paper_2212_04551_gb300 import graphs as G
     gs = list(G.workload("ba4096"))
     b = gpm.batch_from_graphs(gs, stream=stream)
+    t0 = time.perf_counter()
     best, _ = gpm.gpm_batch_autotune(b, 4, 5, reps=3)
+    tune_s = time.perf_counter() - t0
     cc, mc = gpm.gpm_batch_count(b, 4, 5)
     times = []
     for _ in range(reps):
@@ -322,26 +428,99 @@ def batched_vs_plain(stream, reps: int = 5) -> dict:
     parity = None
     gd = golden("ba4096")
     if gd is not None:
-        parity = all(int(cc[i]) == c4 and {str(gpm.gpm_motif_pattern(5, p)): int(x)
-                                           for p, x in enumerate(mc[i]) if x} == m5
+        parity = all(int(cc[i]) == c4 and by_code(5, mc[i]) == m5
                      for i, c4, m5 in zip(gd["graphs"], gd["clique4"], gd["motif5"]))
     t_b = statistics.median(times)
     idle_b = gpm.gpm_batch_get_stats(b)["idle_warp_frac"]
-    # plain: every graph on its own, graphs resident on the device
-    dgs = [gpm.graph_from_csr(g, stream=stream) for g in gs]
-    def plain():
+    # the plain kernel on the disjoint union of all 4,096 graphs
+    u = G.disjoint_union(*gs)
+    du = gpm.graph_from_csr(u, stream=stream)
+    def union():
+        return gpm.gpm_clique_count(du, 4), gpm.gpm_motif_count(du, 5)
+    union()
+    tu = []
+    for _ in range(reps):
+        (uc, um), ms = timed(union, stream)
+        tu.append(ms)
+    assert uc == int(cc.sum()) and np.array_equal(um, mc.sum(axis=0)), "union counts differ from the batch"
+    du.close()
+    # one plain call per graph (graphs resident), warmed
+    dgs = [gpm.graph_from_csr(x, stream=stream) for x in gs]
+    def loop():
         c = np.array([gpm.gpm_clique_count(d, 4) for d in dgs], dtype=np.uint64)
         m = np.stack([gpm.gpm_motif_count(d, 5) for d in dgs])
         return c, m
-    (pc, pm), t_p = timed(plain, stream)
+    loop()
+    tl = []
+    for _ in range(3):
+        (pc, pm), ms = timed(loop, stream)
+        tl.append(ms)
     assert np.array_equal(pc, cc) and np.array_equal(pm, mc), "batched counts differ from per-graph counts"
     for d in dgs:
         d.close()
     b.close()
-    return {"graphs": len(gs), "subgraphs": total, "batched_ms": t_b, "plain_ms": t_p,
-            "batched_subgraphs_per_s": total / (t_b / 1000.0), "plain_subgraphs_per_s": total / (t_p / 1000.0),
-            "speedup": t_p / t_b, "autotuned": best, "batched_idle_warp_frac": idle_b,
+    t_u, t_l = statistics.median(tu), statistics.median(tl)
+    return {"workload": "ba4096: 4,096 BA graphs (n~U[20,400], m_a~U[2,6], seed 3), clique k=4 + motif k=5 per graph",
+            "graphs": len(gs), "subgraphs": total,
+            "batched_ms": t_b, "batched_subgraphs_per_s": total / (t_b / 1000.0),
+            "plain_union_ms": t_u, "plain_union_subgraphs_per_s": total / (t_u / 1000.0),
+            "plain_per_graph_ms": t_l, "plain_per_graph_call_ms": t_l / (2 * len(gs)),
+            "speedup_vs_plain_union": t_u / t_b, "speedup_vs_plain_per_graph": t_l / t_b,
+            "autotuned": best, "autotune_s": round(tune_s, 1), "batched_idle_warp_frac": idle_b,
             "oracle_parity_48_graphs": parity}
+
+
+def config_sbm2000(stream, learned: Learned) -> dict:
+    """Stochastic block model (2,000 vertices, 20 blocks): every clique size
+    6..12 from one enumeration, and 6-vertex motifs plain vs learned."""
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    g = G.workload("sbm2000")
+    dg = gpm.graph_from_csr(g, stream=stream)
+    cr = gpm.gpm_clique_count_range(dg, 6, 12)
+    kms = []
+    for _ in range(3):
+        cr = gpm.gpm_clique_count_range(dg, 6, 12)
+        kms.append(gpm.gpm_get_stats(dg)["kernel_ms"])
+    gd = golden("sbm2000")
+    want = {cs["k"]: cs["total"] for cs in gd["cases"] if cs["app"] == "clique" and cs["roots"] is None} if gd else {}
+    res = {"workload": "sbm2000 (n=2,000, 20 blocks, p_in 0.5, p_out 0.01, seed 4)",
+           "clique_6_12": {"counts": {str(k): int(c) for k, c in zip(range(6, 13), cr)},
+                           "kernel_ms": statistics.median(kms),
+                           "subgraphs_per_s": sum(int(c) for c in cr) / (statistics.median(kms) / 1000.0),
+                           "oracle_parity": all(int(c) == want.get(k) for k, c in zip(range(6, 13), cr))}}
+    cmp6, c6, _ = learned.compare(dg, g, 6, None, reps=1, arms=("plain", "learned", "untrained"))
+    gf = golden("sbm2000_full")
+    want6 = next((cs["patterns"] for cs in gf["cases"] if cs["k"] == 6 and cs["roots"] is None), None) if gf else None
+    res["motif6"] = {"subgraphs": int(c6.sum()), **cmp6, "oracle_parity": by_code(6, c6) == want6 if want6 else None}
+    dg.close()
+    return res
+
+
+def k4_8_entry(dg, g, stream) -> dict:
+    """The configuration's full range: one enumeration to depth 8, timed
+    once, and the 8-cliques of the stored 1/64 heaviest-first root sample
+    checked root by root."""
+    from paper_2212_04551_gb300 import gpm
+    counts, ms = timed(lambda: gpm.gpm_clique_count_range(dg, 4, 8), stream)
+    st = gpm.gpm_get_stats(dg)
+    full = oracle_clique_totals(g)
+    res = {"counts": {str(k): int(c) for k, c in zip(range(4, 9), counts)}, "ms": ms,
+           "kernel_ms": st["kernel_ms"], "subgraphs_per_s": sum(int(c) for c in counts) / (ms / 1000.0),
+           "word_ops": int(st["word_ops"]), "idle_warp_frac": st["idle_warp_frac"],
+           "oracle_parity_full": {str(k): int(c) == full[k] for k, c in zip(range(4, 9), counts) if k in full}}
+    gk = golden("chunglu1m_k78")
+    if gk is not None and gk["sha256"] == g.sha256():
+        sample = heaviest_first(g)[0::64]
+        c8, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, 8, sample, per_root=True)
+        want = np.zeros(g.n, dtype=np.uint64)
+        for r, _, v8 in gk["k8_sample"]["per_root"]:
+            want[r] = v8
+        res["oracle_parity_k8_sample"] = {
+            "roots": int(sample.shape[0]), "rule": gk["k8_sample"]["rule"],
+            "total": int(c8[0]) == gk["k8_sample"]["cliques"]["8"],
+            "per_root": bool(np.array_equal(pr, want[sample]))}
+    return res
 
 
 def main():
@@ -351,26 +530,29 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     from paper_2212_04551_gb300 import graphs as G
 
+    kk = list(range(args.k_lo, args.k_hi + 1))
     config = {"workload": f"chunglu1m clique k={args.k_lo}..{args.k_hi}",
               "graph": "Chung-Lu n=1,000,000 avg deg 16 gamma 2.1 cap 20,000 seed 1, degree-ordered int32 CSR",
-              "k": list(range(args.k_lo, args.k_hi + 1)),
-              "l2": "flushed between timed steps (512 MB write)", "parallelism": f"roots split over {world} rank(s)"}
+              "k": kk, "l2": "flushed between timed steps (512 MB write)",
+              "parallelism": f"roots split over {world} rank(s)"}
 
     if args.impl == "reference":
         if rank != 0:
             return
         g = G.workload("chunglu1m")
         t_start = time.perf_counter()
-        vals = []
-        for _ in range(args.warmup + args.steps):
-            v, desc, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_seconds / max(1, args.steps))
+        vals, descs, cores = [], [], 1
+        for i in range(args.warmup + args.steps):
+            v, desc, cores, _, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_stride * 2, offset=1 + 2 * i)
             vals.append(v)
+            descs.append(desc)
         v = statistics.median(vals[args.warmup:]) if args.steps else vals[-1]
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "ms_per_step": (time.perf_counter() - t_start) * 1000 / max(1, args.warmup + args.steps),
                 "dtype": "int64", "data": "synthetic", "config": config, "vs_baseline": None,
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": descs[-1] + "; one offset per step"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -395,7 +577,6 @@ def main():
     order = np.argsort(-outdeg, kind="stable").astype(np.int32)
     order = order[outdeg[order] >= args.k_lo - 1]          # roots that can hold a k_lo-clique
     my_roots = order[rank::world] if world > 1 else None
-    kk = list(range(args.k_lo, args.k_hi + 1))
 
     def step():
         if my_roots is None:
@@ -464,8 +645,7 @@ def main():
     # counts of candidate words; achieved = word operations per launch (the
     # kernel counts them exactly) / the launch's CUDA-event time
     hbm, sm_max, peak_kind = peaks()
-    import torch as _t
-    sms = _t.cuda.get_device_properties(local_rank).multi_processor_count
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     peak_ops = sms * POPC_PER_CLK_PER_SM * sm_max * 1e6
     wops = statistics.mean(word_ops)
     achieved = wops / (statistics.mean(kern_ms) / 1000.0)
@@ -474,7 +654,7 @@ def main():
                 "unit": "Gop/s (32-bit candidate-word AND+POPC)", "frac": achieved / peak_ops,
                 "peak_kind": f"derived: {sms} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz ({peak_kind} clock)",
                 "units_per_launch": wops,
-                "traffic": profiled_traffic("k_clique_chunglu1m.txt", src_hash, wops),
+                "traffic": profiled_traffic(f"k_clique_chunglu1m_k{args.k_lo}_{args.k_hi}.txt", src_hash, wops),
                 "kernel_source_sha": src_hash}
     # HBM: DRAM bytes of the launch (ncu) over its time -- reported beside the
     # ALU roofline to show that memory bandwidth is not what binds the kernel
@@ -483,20 +663,13 @@ def main():
     hbm_line = {"achieved_gbs": traffic / kern_s / 1e9 if traffic else None, "peak_gbs": hbm,
                 "frac": traffic / kern_s / 1e9 / hbm if traffic else None,
                 "peak_kind": f"{peak_kind} copy bandwidth", "bytes_per_launch": traffic}
-    # parity at full size against the oracle's stored totals, and the bytes a
-    # sorted-list merge enumerator would move for the same search (B_alg),
-    # expressed against the measured HBM bandwidth
-    full = oracle_full_size(args.k_lo, args.k_hi)
+    # parity at full size against the oracle's stored totals
+    full = oracle_clique_totals(g)
     parity = None
-    list_merge = None
-    if full is not None and world == 1 and full["sha256"] == g.sha256():
-        parity = {"oracle_full_size": all(int(c) == full["cliques"][str(k)] for k, c in zip(kk, counts)),
-                  "source": "tests/golden/chunglu1m_full.json (oracle over every root)"}
-        if args.k_hi == full["k_max"]:
-            b = float(full["b_alg_depth6"])
-            list_merge = {"b_alg_bytes_per_step": b, "gbs": b / (t_step / 1000.0) / 1e9,
-                          "x_measured_hbm_peak": b / (t_step / 1000.0) / 1e9 / hbm,
-                          "definition": "sum over node expansions of 4 (|C(S)| + d+(v)) bytes (sorted-list merge)"}
+    if world == 1 and all(k in full for k in kk):
+        parity = {"oracle_full_size": all(int(c) == full[k] for k, c in zip(kk, counts)),
+                  "source": "tests/golden/chunglu1m_full.json (k <= 6) and chunglu1m_k78.json (k = 7): "
+                            "oracle over every root"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -507,17 +680,21 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_ip.nbytes + h_ix.nbytes),
                 "d2h_bytes_per_step": 8 * len(kk), "ms_per_step": statistics.mean(e2e_ms)},
         "clocks": clocks, "gpu_launches": launches,
-        "roofline": roofline, "hbm": hbm_line, "parity": parity, "list_merge_equivalent": list_merge,
+        "roofline": roofline, "hbm": hbm_line, "parity": parity,
         "sm_idle": {"idle_warp_frac": statistics.mean(idle_frac),
                     "definition": "1 - (sum over the grid's warps of time inside work units) / "
                                   "(warps x kernel time), %globaltimer"},
     }
-    if rank == 0 and world == 1 and not args.no_variants:
-        line["batched_vs_plain"] = batched_vs_plain(stream)
-        line["learned_vs_plain"] = learned_vs_plain(stream)
+    if rank == 0 and world == 1 and not args.no_k8:
+        line["k4_8"] = k4_8_entry(dg, g, stream)
+    if rank == 0 and world == 1 and not args.no_configs:
+        learned = Learned(stream)
+        line["learned_training"] = learned.info
+        line["configs"] = {"er516": config_er516(stream), "rmat16": config_rmat16(stream, learned),
+                           "ba4096": config_ba4096(stream), "sbm2000": config_sbm2000(stream, learned)}
     if rank == 0 and not args.no_cpu_baseline:
-        v, desc, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        v, desc, cores, _, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_stride)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -171,6 +171,8 @@ typedef struct {
     int32_t motif_agg_min;     /* motif: a node one level above the leaves whose extension array     */
                                /* has at least this many entries left counts its last two levels by  */
                                /* entry class instead of leaf by leaf (0: never)                     */
+    int32_t clique_compact3;   /* three-level clique tail on the node's members whenever that        */
+                               /* shortens the rows: 1 (default) or 0                                */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */
@@ -352,6 +354,20 @@ gpm_status gpm_batch_get_stats(const gpm_batch* b, gpm_stats* out);
  */
 gpm_status gpm_motif_count_noalloc(const int32_t* indptr, const int32_t* indices, int32_t n, int k,
                                    uint64_t* counts, int64_t counts_len, void* stream);
+
+/*
+ * Self-test of the overflow contract (the paper is silent on overflow; the
+ * library's reading is that a true count >= 2^64 is an error, never a
+ * wrapped value).  Sums n uint64 values (host array) on the device through
+ * the counting kernels' own carry-checked reduction path -- lane-private
+ * adds over a grid-stride loop, warp sums, a per-block shared counter and a
+ * global counter -- with `blocks` x `threads` threads (threads a multiple of
+ * 32), so a caller can place large values in one lane, one warp, one block
+ * or several blocks.  *out = the exact sum when it fits; otherwise the call
+ * returns GPM_EOVERFLOW.  Allocates a temporary device buffer.
+ * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_EOVERFLOW.
+ */
+gpm_status gpm_selftest_sum(const uint64_t* values, int64_t n, int32_t blocks, int32_t threads, uint64_t* out);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* gpm_last_error(void);

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     cw.donate_after_ns = 0;
     cw.tail_levels = 0;
     cw.compact = 0;
+    cw.compact3 = 0;
     // motif part
     unsigned char* mt = base + (size_t)p.cq_words * 4;
     MtWarp* W = reinterpret_cast<MtWarp*>(mt);
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     for (int v = lane; v < p.mark_stride; v += 32) marks[v] = 0;
     for (int j = lane; j < p.npat; j += 32) wc[j] = 0ull;
     __syncwarp();
-    WarpSink sink{wc};
+    WarpSink sink{wc, &p.ctl->overflow};
     int cached_root = -1;
     Control* ctl = p.ctl;
     unsigned long long busy = 0;      // time spent inside work units (%globaltimer ns)
@@ -178,10 +179,11 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
             __syncwarp();
             unsigned long long km1 = 0, wops = 0;
             cq_walk<false>(cw, unit, 0, r, d, cached_root, sum, km1, wops, lane);
-            sum = gpm_warp_sum(sum);
-            if (lane == 0 && sum) {
-                const unsigned long long old = atomicAdd(&p.clique_out[gidx], sum);
-                if (old + sum < old) atomicExch(&ctl->overflow, 1);
+            int ovf = 0;
+            sum = gpm_warp_sum_cc(sum, ovf);
+            if (lane == 0) {
+                if (ovf) atomicExch(&ctl->overflow, 1);
+                gpm_atomic_add_cc(&p.clique_out[gidx], sum, &ctl->overflow);
             }
         } else {
             // ---- motif unit

@@ -226,6 +226,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.clique_tail != 0 && c.clique_tail != 2 && c.clique_tail != 3) fail(GPM_EINVAL, "clique_tail must be 0, 2 or 3");
         if (c.clique_compact < 0 || c.clique_compact > 2) fail(GPM_EINVAL, "clique_compact must be 0, 1 or 2");
         if (c.motif_agg_min < 0) fail(GPM_EINVAL, "motif_agg_min < 0");
+        if (c.clique_compact3 != 0 && c.clique_compact3 != 1) fail(GPM_EINVAL, "clique_compact3 must be 0 or 1");
         g->cfg = c;
     });
 }

@@ -67,13 +67,14 @@ struct CliqueParams {
     unsigned long long max_idle_ns;
     int tail_levels;
     int compact;
+    int compact3;
 };
 
 __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0);
+    const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0 || p.compact3 != 0);
     uint32_t* base = smem + (size_t)wib * p.stride_words;
     unsigned long long* wcnt = reinterpret_cast<unsigned long long*>(base + L.wcnt);
     CliqueUnit* unit = reinterpret_cast<CliqueUnit*>(base + L.unit);
@@ -111,7 +112,9 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     walk.donate_after_ns = p.donate_after_ns;
     walk.tail_levels = p.tail_levels;
     walk.compact = p.compact;
+    walk.compact3 = p.compact3;
 
+    int ovf = 0;                      // a carry-checked sum wrapped (lane-private)
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
     unsigned long long top_km1 = 0;   // lane-private (k_hi-1)-clique count
     unsigned long long wops = 0;      // lane-private candidate-word operations
@@ -216,10 +219,10 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         const bool ok = p.donate ? cq_walk<true>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane)
                                  : cq_walk<false>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane);
         if (!ok) aborted = true;
-        top_sum += unit_sum;
+        top_sum = gpm_add_cc(top_sum, unit_sum, ovf);
         if (p.per_root) {
-            const unsigned long long tot = gpm_warp_sum(unit_sum);
-            if (lane == 0 && tot) atomicAdd(&p.per_root[root_pos], tot);
+            const unsigned long long tot = gpm_warp_sum_cc(unit_sum, ovf);
+            if (lane == 0) gpm_atomic_add_cc(&p.per_root[root_pos], tot, &ctl->overflow);
         }
         __syncwarp();
         if (lane == 0) {
@@ -229,11 +232,12 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         busy += gpm_globaltimer() - t_unit;
     }
 
-    const unsigned long long tot = gpm_warp_sum(top_sum);
-    const unsigned long long km1 = gpm_warp_sum(top_km1);
+    const unsigned long long tot = gpm_warp_sum_cc(top_sum, ovf);
+    const unsigned long long km1 = gpm_warp_sum_cc(top_km1, ovf);
     const unsigned long long wsum = gpm_warp_sum(wops);
     __syncwarp();
     if (lane == 0) {
+        if (ovf) atomicExch(&ctl->overflow, 1);
         atomicAdd(&ctl->word_ops, wsum);
         if (polls) atomicAdd(&ctl->idle_polls, polls);
         atomicAdd(&ctl->busy_ns, busy);
@@ -327,7 +331,10 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         p.maxd = std::max(g->max_outdeg, 1);
         p.wmax = (p.maxd + 31) / 32;
         p.compact = g->cfg.clique_compact;   // before the layout: it sizes the compaction region
-        const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0);
+        // the compacted three-level tail runs where the three-level tail does
+        const bool three = k_hi >= 5 && (g->cfg.clique_tail == 3 || (g->cfg.clique_tail == 0 && k_hi >= 7));
+        p.compact3 = (three && g->cfg.clique_compact3) ? 1 : 0;
+        const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0 || p.compact3 != 0);
         p.stride_words = L.total;
         int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block
                                               : best_warps_per_block((const void*)k_clique, (size_t)L.total * 4, 0);

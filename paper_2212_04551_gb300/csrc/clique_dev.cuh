@@ -45,12 +45,12 @@ static_assert(sizeof(CliqueUnit) % 4 == 0, "unit must be word-sized");
 
 
 
-// words of the pair / compacted-matrix region: the pair batch, or (with the
+// words of the pair / compacted-matrix region: the pair batch, or (with a
 // compacted tail on and rows of at least three words) up to 32 * CQ_CW
-// members x CQ_CW words
+// members x CQ_CW words followed by a pair batch over them
 __host__ __device__ inline int cq_pairs_words(int wmax, bool compact) {
     const int pairs = CQ_PAIR_FLUSH + 32 * wmax;
-    const int cm = (compact && wmax >= 3) ? min(32 * wmax, 32 * CQ_CW) * CQ_CW : 0;
+    const int cm = (compact && wmax >= 3) ? 32 * CQ_CW * CQ_CW + CQ_PAIR_FLUSH + 32 * CQ_CW : 0;
     return pairs > cm ? pairs : cm;
 }
 
@@ -129,9 +129,15 @@ __device__ __forceinline__ int count_range(const uint32_t* C, int w, int from, i
 }
 
 __device__ __forceinline__ void add_count(Control* ctl, int j, unsigned long long v) {
-    if (!v) return;
-    const unsigned long long old = atomicAdd(&ctl->counts[j], v);
-    if (old + v < old) atomicExch(&ctl->overflow, 1);
+    gpm_atomic_add_cc(&ctl->counts[j], v, &ctl->overflow);
+}
+
+// add to one of the warp's per-size counters (lane 0), raising the launch's
+// overflow flag if it wraps
+__device__ __forceinline__ void cq_wadd(Control* ctl, unsigned long long* c, unsigned long long v) {
+    const unsigned long long s = *c + v;
+    if (s < *c) atomicExch(&ctl->overflow, 1);
+    *c = s;
 }
 
 // Build the root-local bit matrix.  The out-neighbours u of r get local
@@ -215,6 +221,7 @@ struct CliqueWalk {
     unsigned long long donate_after_ns;   // a unit splits only after running this long
     int tail_levels;                      // 2 or 3 (0: 3)
     int compact;                          // compacted two-level tail: 0 never, 1 large nodes, 2 whenever shorter
+    int compact3;                         // compacted three-level tail whenever it shortens the rows
     __device__ uint32_t* pairs_u32() const { return reinterpret_cast<uint32_t*>(pairs); }
 };
 
@@ -498,6 +505,115 @@ __device__ __forceinline__ void cq_tail3_dispatch(const uint32_t* C, const TriRo
     else cq_tail3<10>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
 }
 
+// The last three levels below a node of size k-4, on the node's own members
+// (as cq_tail2c does for two): member m is the m-th set bit of C, and R[m]
+// holds the members adjacent to m above it, ceil(c/32) words per row instead
+// of ceil(d/32).  The node's children (members with positions in [from,
+// to)) are walked in order; the grandchildren m2 of each m1 (bits of R[m1])
+// go to a pair batch, run lane-parallel: C_m1m2 = R[m1] & R[m2] (its
+// popcount: the (k-1)-cliques through the pair), then popc(C_m1m2 & R[l])
+// for every l in it (the k-cliques).  mem: c ints; R: c x (W2 | 1) words,
+// then the pair batch.  Uniform counts: n3 children, n2 pairs.
+template <int W2>
+__device__ __forceinline__ void cq_pairs_run_c(const uint32_t* R, int ws2, int w2, const int* pairs, int np,
+                                               unsigned long long& km1, unsigned long long& kk,
+                                               unsigned long long& wops, int lane) {
+    for (int t = lane; t < np; t += 32) {
+        const int pr = pairs[t];
+        const uint32_t* r1 = R + (pr >> 16) * ws2;
+        const uint32_t* r2 = R + (pr & 0xffff) * ws2;
+        uint32_t x[W2];
+        int g = 0;
+#pragma unroll
+        for (int z = 0; z < W2; z++) {
+            x[z] = z < w2 ? (r1[z] & r2[z]) : 0u;
+            g += __popc(x[z]);
+        }
+        km1 += (unsigned)g;
+        wops += (unsigned long long)(g + 1) * (unsigned)w2;
+        kk += cq_sum_rows<W2>(x, RectRows{R, ws2}, w2);
+    }
+}
+
+template <int W2>
+__device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows, int w, int c, int from, int to,
+                                          int* mem, uint32_t* R, unsigned long long& n3, unsigned long long& n2,
+                                          unsigned long long& km1, unsigned long long& kk,
+                                          unsigned long long& wops, int lane) {
+    int n = 0, m_lo = 0, m_hi = 0;
+    for (int q = 0; q < w; q++) {
+        const uint32_t word = C[q];
+        const bool bit = (word >> lane) & 1u;
+        const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
+        if (bit) mem[n + __popc(bal & gpm_lanemask_lt())] = 32 * q + lane;
+        n += __popc(bal);
+        m_lo += __popc(bal & range_mask(q, 0, from));
+        m_hi += __popc(bal & range_mask(q, 0, to));
+    }
+    __syncwarp();
+    const int w2 = (c + 31) >> 5;
+    const int ws2 = w2 | 1;
+    int* pairs = reinterpret_cast<int*>(R + 32 * CQ_CW * CQ_CW);
+    int pm[W2];
+#pragma unroll
+    for (int b = 0; b < W2; b++) pm[b] = (b < w2 && 32 * b + lane < c) ? mem[32 * b + lane] : -1;
+    for (int m = 0; m < c; m++) {
+        const int pmm = mem[m];
+        const uint32_t* row = rows.row(pmm);
+        uint32_t* Rm = R + m * ws2;
+#pragma unroll
+        for (int b = 0; b < W2; b++) {
+            if (b < w2) {
+                uint32_t word = 0u;
+                if (b >= (m >> 5)) {      // members above m only: earlier words are empty
+                    const bool bit = pm[b] > pmm && ((row[pm[b] >> 5] >> (pm[b] & 31)) & 1u);
+                    word = __ballot_sync(GPM_FULL_MASK, bit);
+                }
+                if (lane == b) Rm[b] = word;
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) wops += (unsigned long long)c * (unsigned)w2;
+    n3 += (unsigned)(m_hi - m_lo);
+    int np = 0;
+    for (int m1 = m_lo; m1 < m_hi; m1++) {
+        const uint32_t* r1 = R + m1 * ws2;
+        for (int q2 = m1 >> 5; q2 < w2; q2++) {
+            const uint32_t word = r1[q2];
+            const bool bit = (word >> lane) & 1u;
+            const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
+            if (bit) pairs[np + __popc(bal & gpm_lanemask_lt())] = (m1 << 16) | (32 * q2 + lane);
+            np += __popc(bal);
+        }
+        if (np >= CQ_PAIR_FLUSH) {
+            __syncwarp();
+            n2 += (unsigned)np;
+            cq_pairs_run_c<W2>(R, ws2, w2, pairs, np, km1, kk, wops, lane);
+            __syncwarp();
+            np = 0;
+        }
+    }
+    if (np) {
+        __syncwarp();
+        n2 += (unsigned)np;
+        cq_pairs_run_c<W2>(R, ws2, w2, pairs, np, km1, kk, wops, lane);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void cq_tail3c_dispatch(const uint32_t* C, const TriRows& rows, int w, int c, int from,
+                                                   int to, int* mem, uint32_t* R, unsigned long long& n3,
+                                                   unsigned long long& n2, unsigned long long& km1,
+                                                   unsigned long long& kk, unsigned long long& wops, int lane) {
+    const int w2 = (c + 31) >> 5;
+    if (w2 <= 1) cq_tail3c<1>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
+    else if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
+    else if (w2 <= 3) cq_tail3c<3>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
+    else if (w2 <= 4) cq_tail3c<4>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
+    else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
+}
+
 // Walk one unit (root r = roots[root_pos], d = |N+(r)|).  Returns false if it
 // stopped on a device error.  Lane-private results: unit_sum (k_hi-cliques)
 // and km1 (k_hi-1 cliques, used when k_lo < k_hi); smaller sizes go to wcnt.
@@ -547,10 +663,17 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         const uint32_t* Cs = cand + s * a.wmax;
         if (s == tail && three) {
             unsigned long long n3 = 0, n2 = 0;
-            cq_tail3_dispatch(Cs, rows, w, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
+            // on the node's members when that shortens the rows
+            const int c = (w >= 3 && a.compact3) ? count_range(Cs, w, 0, d, lane) : 0;
+            const int w2 = (c + 31) >> 5;
+            if (c > 0 && w2 <= CQ_CW && w2 < w)
+                cq_tail3c_dispatch(Cs, rows, w, c, cur[s], hiv[s], list, a.pairs_u32(), n3, n2, km1, unit_sum, wops,
+                                   lane);
+            else
+                cq_tail3_dispatch(Cs, rows, w, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
             if (lane == 0) {
-                if (K - 3 >= a.k_lo) wcnt[K - 3] += n3;
-                if (K - 2 >= a.k_lo) wcnt[K - 2] += n2;
+                if (K - 3 >= a.k_lo) cq_wadd(a.ctl, &wcnt[K - 3], n3);
+                if (K - 2 >= a.k_lo) cq_wadd(a.ctl, &wcnt[K - 2], n2);
             }
             __syncwarp();
             if (s == s_base) break;
@@ -565,7 +688,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                 unsigned long long nch = 0;
                 cq_tail2c_dispatch(Cs, rows, w, c, cur[s], hiv[s], list, a.pairs_u32(), nch, km1, unit_sum,
                                    wops, lane);
-                if (lane == 0 && K - 2 >= a.k_lo) wcnt[K - 2] += nch;
+                if (lane == 0 && K - 2 >= a.k_lo) cq_wadd(a.ctl, &wcnt[K - 2], nch);
                 __syncwarp();
                 if (s == s_base) break;
                 s--;
@@ -587,7 +710,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                 }
                 unit_sum += sum;
             } else {
-                if (lane == 0 && K - 2 >= a.k_lo) wcnt[K - 2] += (unsigned)nchild;
+                if (lane == 0 && K - 2 >= a.k_lo) cq_wadd(a.ctl, &wcnt[K - 2], (unsigned)nchild);
                 cq_tail2_dispatch(Cs, rows, w, list, nchild, km1, unit_sum, wops, lane);
             }
             __syncwarp();
@@ -611,7 +734,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         if (lane == 0) wops += (unsigned)w;
         if (lane == 0) {
             cur[s] = i + 1;
-            if (s + 1 >= a.k_lo) wcnt[s + 1] += 1ull;
+            if (s + 1 >= a.k_lo) cq_wadd(a.ctl, &wcnt[s + 1], 1ull);
         }
         // descend while the child can still reach a counted size
         const bool down = c > 0 && (s + 1 + c >= a.k_lo);

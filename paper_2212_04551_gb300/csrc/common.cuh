@@ -226,6 +226,33 @@ __device__ __forceinline__ T gpm_warp_sum(T v) {
     return v;
 }
 
+// Carry-checked counting.  Counts are non-negative, so a partial sum that
+// wraps means the true total is >= 2^64: the helpers below raise a flag
+// instead of letting a wrapped value through (the GPM_EOVERFLOW contract).
+// Inner-loop lane accumulators are not checked: each of their adds is below
+// 2^16 and they are reset per work unit, so one would have to run for years
+// to wrap; every add from a unit upwards goes through these helpers.
+__device__ __forceinline__ unsigned long long gpm_add_cc(unsigned long long a, unsigned long long b, int& ovf) {
+    const unsigned long long s = a + b;
+    ovf |= s < a ? 1 : 0;
+    return s;
+}
+
+// Sum over the warp (every lane gets it); ovf is raised in every lane when
+// any partial sum wrapped.
+__device__ __forceinline__ unsigned long long gpm_warp_sum_cc(unsigned long long v, int& ovf) {
+    for (int o = 16; o > 0; o >>= 1) v = gpm_add_cc(v, __shfl_xor_sync(GPM_FULL_MASK, v, o), ovf);
+    ovf = __any_sync(GPM_FULL_MASK, ovf) ? 1 : 0;
+    return v;
+}
+
+// Atomic add into a (shared or global) counter; *flag = 1 if it wrapped.
+__device__ __forceinline__ void gpm_atomic_add_cc(unsigned long long* c, unsigned long long v, int* flag) {
+    if (!v) return;
+    const unsigned long long old = atomicAdd(c, v);
+    if (old + v < old) atomicExch(flag, 1);
+}
+
 // ------------------------------------------------- donation queue (device)
 //
 // Bounded multi-producer multi-consumer ring of sequence-numbered slots

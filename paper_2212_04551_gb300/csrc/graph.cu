@@ -382,6 +382,7 @@ gpm_config default_config() {
     c.clique_tail = 0;
     c.clique_compact = 0;
     c.motif_agg_min = 16;
+    c.clique_compact3 = 1;
     return c;
 }
 

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         a.slab = p.slab + gw * p.slab_ints;
     }
     __syncthreads();
-    BlockSink sink{bcnt};
+    BlockSink sink{bcnt, &ctl->overflow};
     const int32_t* __restrict__ indptr = p.indptr;
     const int32_t* __restrict__ indices = p.indices;
 
@@ -216,8 +216,12 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         mt_clear_prefix(a, W, pdepth, lane);
 
         if (p.per_root) {
-            const unsigned long long tot = gpm_warp_sum(unit_leaves);
-            if (lane == 0 && tot) atomicAdd(&p.per_root[root_pos], tot);
+            int ovf = 0;
+            const unsigned long long tot = gpm_warp_sum_cc(unit_leaves, ovf);
+            if (lane == 0) {
+                if (ovf) atomicExch(&ctl->overflow, 1);
+                gpm_atomic_add_cc(&p.per_root[root_pos], tot, &ctl->overflow);
+            }
         }
         if (lane == 0) {
             atomicAdd(&ctl->units_done, 1ull);
@@ -230,13 +234,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     if (lane == 0) atomicAdd(&ctl->busy_ns, busy);
     if (lane == 0 && scanned) atomicAdd(&ctl->word_ops, scanned);
     __syncthreads();
-    for (int j = threadIdx.x; j < p.npat; j += blockDim.x) {
-        const unsigned long long v = bcnt[j];
-        if (v) {
-            const unsigned long long old = atomicAdd(&p.counts[j], v);
-            if (old + v < old) atomicExch(&ctl->overflow, 1);
-        }
-    }
+    for (int j = threadIdx.x; j < p.npat; j += blockDim.x) gpm_atomic_add_cc(&p.counts[j], bcnt[j], &ctl->overflow);
 }
 
 // Pre-split seeds: root j of [n_counter, n_counter + n_split) is cut into
@@ -355,11 +353,10 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     const bool smem_state =
         warp_state <= 12 * 1024 && fixed_smem + 8 * (sizeof(MtWarp) + agg_bytes + warp_state) <= 200 * 1024;
     const size_t per_warp = sizeof(MtWarp) + agg_bytes + (smem_state ? (size_t)p.smem_warp_bytes : 0);
-    // Marks in HBM (large graphs): every warp owns n mark bytes that each
-    // leaf reads at random, so the grid is kept small enough for all the
-    // marks to stay in L2 (about 80 MB of them; never below 8 warps per SM):
-    // measured on rmat16 (n = 65,536, k = 5), 1,216 warps run 1.9x faster
-    // than the 4,864 the occupancy limit allows.
+    // Marks in HBM (large graphs): every warp owns n mark bytes.  The grid
+    // fills the SMs (the class-counted last levels are latency-bound and want
+    // every resident warp: rmat16 k = 4, 186 ms at 4,864 warps against 317 ms
+    // at 1,216), up to 8 GB of marks in all.
     int wpb = g->cfg.warps_per_block > 0
                   ? g->cfg.warps_per_block
                   : best_warps_per_block(smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>,
@@ -370,8 +367,8 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     // 17.9 s at 4 warps per block, 21.5 s at 16).
     if (smem_state && g->cfg.warps_per_block <= 0) wpb = std::min(wpb, 4);
     if (!smem_state && g->cfg.warps_per_block <= 0 && g->cfg.blocks_per_sm <= 0) {
-        const long long l2_warps = (80ll << 20) / std::max<long long>(g->n, 1);
-        const long long per_sm_warps = std::max<long long>(8, l2_warps / std::max(g->num_sms, 1));
+        const long long mark_warps = (8ll << 30) / std::max<long long>(g->n, 1);
+        const long long per_sm_warps = std::max<long long>(8, mark_warps / std::max(g->num_sms, 1));
         wpb = 4;
         max_per_sm = (int)std::max<long long>(2, per_sm_warps / wpb);
     }

@@ -34,6 +34,7 @@ constexpr int MT_MAXK = GPM_MOTIF_MAX_K;
 constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns
 constexpr unsigned long long MT_CHECK_NS = 4000;  // busy warps look for idle ones at most this often
 constexpr float MT_MIN_DONATE_WORK = 2048.f;    // estimated leaves a handed-over range must carry
+constexpr int MT_AGG_UNROLL = 4;                 // adjacency entries per lane per round (mt_tail_agg)
 
 // A work unit: the children at positions [lo, hi) of the extension array of
 // the node tr = (sub[0], .., sub[depth-1]) (hi < 0: all of them).  The node's
@@ -97,16 +98,19 @@ __host__ __device__ constexpr int mt_agg_words(int k) {
 
 __device__ __forceinline__ int mt_code_off(int i) { return i * (i - 1) / 2 - 1; }   // bits of v_i, i >= 2
 
-// Shared counters of one block (single-graph kernel).
+// Shared counters of one block (single-graph kernel); ovf: the launch's
+// overflow flag, raised if a counter wraps.
 struct BlockSink {
     unsigned long long* c;
-    __device__ __forceinline__ void add(int pid, unsigned long long v) { atomicAdd(&c[pid], v); }
+    int* ovf;
+    __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }
 };
 
 // Per-warp counters of the current unit (batched kernel), flushed per unit.
 struct WarpSink {
     unsigned long long* c;
-    __device__ __forceinline__ void add(int pid, unsigned long long v) { atomicAdd(&c[pid], v); }
+    int* ovf;
+    __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }
 };
 
 // one leaf per active lane under pattern pid: one add per distinct pattern
@@ -410,33 +414,54 @@ __device__ __noinline__ void mt_tail_agg(const MotifWalk& a, MtWarp* W, int l, c
         const int pre = incl - len;
         const int total = __shfl_sync(GPM_FULL_MASK, incl, 31);
         if (lane == 0) scanned += (unsigned)total;
-        for (int f0 = 0; f0 < total; f0 += 32) {
-            const int f = f0 + lane;
-            int t = 0;                           // owner: the last lane with pre <= f
+        // MT_AGG_UNROLL entries per lane per round, their loads issued
+        // together (the mark loads are random and latency-bound)
+        for (int f0 = 0; f0 < total; f0 += 32 * MT_AGG_UNROLL) {
+            int xs[MT_AGG_UNROLL], wts[MT_AGG_UNROLL], sts[MT_AGG_UNROLL];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int pc = __shfl_sync(GPM_FULL_MASK, pre, t + step);
-                if (pc <= f) t += step;
+            for (int u = 0; u < MT_AGG_UNROLL; u++) {
+                const int f = f0 + 32 * u + lane;
+                int t = 0;                       // owner: the last lane with pre <= f
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int pc = __shfl_sync(GPM_FULL_MASK, pre, t + step);
+                    if (pc <= f) t += step;
+                }
+                wts[u] = __shfl_sync(GPM_FULL_MASK, w, t);
+                sts[u] = __shfl_sync(GPM_FULL_MASK, sw, t);
+                const int bt = __shfl_sync(GPM_FULL_MASK, b, t);
+                const int pt = __shfl_sync(GPM_FULL_MASK, pre, t);
+                xs[u] = f < total ? a.indices[bt + (f - pt)] : -1;
             }
-            const int wt = __shfl_sync(GPM_FULL_MASK, w, t);
-            const int st = __shfl_sync(GPM_FULL_MASK, sw, t);
-            const int bt = __shfl_sync(GPM_FULL_MASK, b, t);
-            const int pt = __shfl_sync(GPM_FULL_MASK, pre, t);
-            int ke = -1, kp = -1;
-            if (f < total) {
-                const int x = a.indices[bt + (f - pt)];
-                const unsigned char m = a.mk[x - a.mbase];
-                if ((m & (lowtr | 0x80u)) == 0) {
-                    ke = st;                     // exclusive neighbour of w
-                } else if ((m & 0x40) && ((m & 0x20) || x > wt)) {
-                    const int s2 = m & lowtr;    // adjacent pair of entries
-                    kp = min(st, s2) * C + max(st, s2);
+            unsigned char ms[MT_AGG_UNROLL];
+#pragma unroll
+            for (int u = 0; u < MT_AGG_UNROLL; u++) ms[u] = xs[u] >= 0 ? a.mk[xs[u] - a.mbase] : (unsigned char)0;
+#pragma unroll
+            for (int u = 0; u < MT_AGG_UNROLL; u++) {
+                bool ex = false;
+                if (xs[u] >= 0) {
+                    const unsigned m = ms[u];
+                    if ((m & (lowtr | 0x80u)) == 0) {
+                        ex = true;                   // exclusive neighbour of w
+                    } else if ((m & 0x40u) && ((m & 0x20u) || xs[u] > wts[u])) {
+                        const int s2 = (int)(m & lowtr);   // adjacent pair of entries (rare)
+                        atomicAdd(&P[min(sts[u], s2) * C + max(sts[u], s2)], 1u);
+                    }
+                }
+                // exclusive neighbours per child: the lanes of one child are
+                // contiguous, so the first lane of each child's run adds the
+                // run's count (children of one class may share a counter)
+                const unsigned exm = __ballot_sync(GPM_FULL_MASK, ex);
+                const int wprev = __shfl_up_sync(GPM_FULL_MASK, wts[u], 1);
+                const bool head = xs[u] >= 0 && (lane == 0 || wprev != wts[u]);
+                const unsigned heads = __ballot_sync(GPM_FULL_MASK, head);
+                if (head) {
+                    const unsigned later = heads & ~((2u << lane) - 1u);   // heads above this lane
+                    const unsigned run = (later ? ((1u << (__ffs(later) - 1)) - 1u) : 0xffffffffu) & ~((1u << lane) - 1u);
+                    const unsigned cnt = (unsigned)__popc(exm & run);
+                    if (cnt) atomicAdd(&E[sts[u]], cnt);
                 }
             }
-            unsigned grp = __match_any_sync(GPM_FULL_MASK, ke);
-            if (ke >= 0 && lane == __ffs(grp) - 1) E[ke] += (uint32_t)__popc(grp);
-            grp = __match_any_sync(GPM_FULL_MASK, kp);
-            if (kp >= 0 && lane == __ffs(grp) - 1) P[kp] += (uint32_t)__popc(grp);
         }
     }
     __syncwarp();

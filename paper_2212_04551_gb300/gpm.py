@@ -45,7 +45,8 @@ class gpm_config(ctypes.Structure):
                 ("donate_min", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
                 ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32),
-                ("clique_compact", ctypes.c_int32), ("motif_agg_min", ctypes.c_int32)]
+                ("clique_compact", ctypes.c_int32), ("motif_agg_min", ctypes.c_int32),
+                ("clique_compact3", ctypes.c_int32)]
 
 
 class gpm_stats(ctypes.Structure):
@@ -94,6 +95,7 @@ SIGNATURES = {
     "gpm_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
     "gpm_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
     "gpm_motif_count_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, _u64p, ctypes.c_int64, _vp]),
+    "gpm_selftest_sum": (ctypes.c_int, [_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _u64p]),
 }
 GPM_MLP_PARAMS = 4801
 
@@ -426,6 +428,7 @@ def gpm_batch_set_config(b: Batch, **kw) -> None:
     c.donate = 1
     c.donate_after_us = 50
     c.motif_agg_min = 16
+    c.clique_compact3 = 1
     for key, val in kw.items():
         setattr(c, key, int(val))
     _check(load().gpm_batch_set_config(b, ctypes.byref(c)), "gpm_batch_set_config")
@@ -462,3 +465,13 @@ def gpm_motif_count_noalloc(indptr, indices, n: int, k: int, stream=None) -> np.
                                           indices.numel() else None, int(n), int(k), out.ctypes.data_as(_u64p),
                                           npat, _stream_handle(stream)), "gpm_motif_count_noalloc")
     return out
+
+
+def gpm_selftest_sum(values, blocks: int = 1, threads: int = 32) -> int:
+    """Exact device sum of uint64 values through the kernels' carry-checked
+    reduction path (GpmError with GPM_EOVERFLOW when it exceeds 2^64-1)."""
+    v = np.ascontiguousarray(values, dtype=np.uint64)
+    out = ctypes.c_uint64()
+    _check(load().gpm_selftest_sum(v.ctypes.data_as(_u64p), int(v.shape[0]), int(blocks), int(threads),
+                                   ctypes.byref(out)), "gpm_selftest_sum")
+    return out.value

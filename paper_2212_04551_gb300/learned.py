@@ -16,13 +16,20 @@ gpm_sched_from_scores, gpm_count_*); torch provides device memory.
 """
 from __future__ import annotations
 
+import base64
+import json
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
 
 from . import gpm
 from . import graphs as G
+
+# Trained weights shipped with the package (written by ``python -m
+# paper_2212_04551_gb300.learned``): FP32 masters plus the record of the run.
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "motif_rmat12_k56.json")
 
 D_IN, D_H = 8, 64
 SHAPES = [("W1", (D_H, D_IN)), ("b1", (D_H,)), ("W2", (D_H, D_H)), ("b2", (D_H,)), ("w3", (D_H,)), ("b3", (1,))]
@@ -151,3 +158,64 @@ def schedule(dg, app: int, pred_vertex, roots=None, warps: int = 4864, chunks: i
     n_split = split_plan(sel, warps, chunks)
     gpm.gpm_sched_from_scores(dg, app, pred_vertex.contiguous(), roots, n_split, chunks if n_split else 0)
     return {"split_roots": n_split, "chunks": chunks if n_split else 0}
+
+
+def save(model: Model, path: str, record: dict) -> None:
+    """FP32 master weights (little-endian, base64) and the training record."""
+    master = model.master.detach().float().cpu().numpy().astype("<f4")
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump({"params": gpm.GPM_MLP_PARAMS, "master_f32_b64": base64.b64encode(master.tobytes()).decode(),
+                   "record": record}, f, indent=1)
+
+
+def load(path: str = WEIGHTS, stream=None):
+    """(Model, training record) from a file written by ``save``."""
+    import torch
+    with open(path) as f:
+        d = json.load(f)
+    master = np.frombuffer(base64.b64decode(d["master_f32_b64"]), dtype="<f4").astype(np.float32)
+    if master.shape[0] != gpm.GPM_MLP_PARAMS:
+        raise ValueError("weight file does not match the network")
+    model = new_model(0, stream)
+    model.master.copy_(torch.from_numpy(master.copy()))
+    zero = torch.zeros_like(model.master)
+    gpm.gpm_mlp_adam(model.master, torch.zeros_like(zero), torch.zeros_like(zero), zero, 1, 0.0, model.w, stream)
+    return model, d["record"]
+
+
+def main(argv=None) -> None:
+    """Train the motif subtree-size network on sizes the plain enumerator
+    measures (every root of R-MAT scale-12 graphs, seeds 100-131, k = 5 and
+    6) and write it to ``--out``."""
+    import argparse
+    import time
+
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--k", type=int, nargs="+", default=[5, 6])
+    ap.add_argument("--seeds", type=int, nargs=2, default=[100, 132])
+    ap.add_argument("--scale", type=int, default=12)
+    ap.add_argument("--epochs", type=int, default=60)
+    a = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    X, T = training_set(gpm.GPM_APP_MOTIF, a.k, seeds=range(*a.seeds), scale=a.scale, stream=stream)
+    label_s = time.perf_counter() - t0
+    model = new_model(0, stream)
+    t0 = time.perf_counter()
+    train(model, X, T, epochs=a.epochs, batch=4096, lr=3e-3, stream=stream)
+    torch.cuda.synchronize()
+    record = {"app": "motif", "k": a.k, "graphs": f"R-MAT scale {a.scale}, edge factor 8, seeds "
+              f"{a.seeds[0]}-{a.seeds[1] - 1}", "samples": int(X.shape[0]), "epochs": a.epochs,
+              "label_s": round(label_s, 1), "train_s": round(time.perf_counter() - t0, 2),
+              "first_mse": model.history[0], "final_mse": model.history[-1],
+              "device": torch.cuda.get_device_name(0)}
+    save(model, a.out, record)
+    print(json.dumps(record))
+
+
+if __name__ == "__main__":
+    main()

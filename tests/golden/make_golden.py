@@ -302,6 +302,82 @@ def write_full(pool, fname):
     print(fname, [(c["k"], c["total"], c["oracle_s"]) for c in cases], flush=True)
 
 
+RMAT_BANDS = [(1, 4), (4, 16), (16, 64), (64, 256), (256, 1024), (1024, 1 << 30)]
+RMAT_PER_BAND = 16
+RMAT_ROOT_LIMIT_S = 150
+
+
+def rmat_strat_candidates(g, k):
+    """Candidate roots of the stratified rmat16 sample at size k: up to 16
+    seeded roots from each band of up-degree (neighbours above the root, the
+    size of its first extension set): 1-3, 4-15, 16-63, 64-255, 256-1023,
+    1024 and more."""
+    ip, ix = g.indptr, g.indices
+    src = np.repeat(np.arange(g.n), np.diff(ip))
+    up = np.bincount(src[ix > src], minlength=g.n)
+    rng = np.random.default_rng(60 + k)
+    out = []
+    for lo, hi in RMAT_BANDS:
+        pool = np.nonzero((up >= lo) & (up < hi))[0]
+        pick = rng.choice(pool, size=min(RMAT_PER_BAND, pool.shape[0]), replace=False) if pool.shape[0] else []
+        out.extend((int(lo), int(r)) for r in sorted(int(x) for x in pick))
+    return out
+
+
+def one_root(name, k, r):
+    """Child-process mode: the ESU-route motif counts of one root, as JSON."""
+    g = G.workload(name)
+    pats, pr = O.motif_count(g, k, roots=np.array([r], dtype=np.int32), per_root=True, method="esu")
+    print(json.dumps({"patterns": {str(c): int(v) for c, v in pats.items()}, "total": int(pr[0])}))
+
+
+def write_rmat16_strat():
+    """rmat16 motif counts at k = 5, 6, 7 on stratified root samples (see
+    rmat_strat_candidates): every candidate runs through the oracle's ESU
+    route in its own process, and a root whose run takes longer than
+    RMAT_ROOT_LIMIT_S seconds is left out (listed under "dropped") -- so the
+    sample holds the heaviest roots the oracle can finish."""
+    import subprocess
+    g = G.workload("rmat16")
+    tasks = [(k, band, r) for k in (5, 6, 7) for band, r in rmat_strat_candidates(g, k)]
+    tasks.sort(key=lambda t: (t[1], t[0]))          # light bands first
+
+    def run(task):
+        k, band, r = task
+        t = time.time()
+        try:
+            p = subprocess.run([sys.executable, os.path.abspath(__file__), "--one-root", "rmat16", str(k), str(r)],
+                               capture_output=True, text=True, timeout=RMAT_ROOT_LIMIT_S)
+        except subprocess.TimeoutExpired:
+            return task, None, round(time.time() - t, 1)
+        if p.returncode != 0:
+            raise RuntimeError(p.stderr)
+        return task, json.loads(p.stdout.strip().splitlines()[-1]), round(time.time() - t, 1)
+
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=max(1, (os.cpu_count() or 1) - 1)) as ex:
+        res = list(ex.map(run, tasks))
+    cases = []
+    for k in (5, 6, 7):
+        done = sorted((t[2], out, secs) for t, out, secs in res if t[0] == k and out is not None)
+        dropped = sorted(t[2] for t, out, _ in res if t[0] == k and out is None)
+        pats: dict = {}
+        for _, out, _ in done:
+            for c, v in out["patterns"].items():
+                pats[c] = pats.get(c, 0) + v
+        cases.append({"app": "motif", "k": k, "roots": [r for r, _, _ in done],
+                      "per_root": [out["total"] for _, out, _ in done],
+                      "total": sum(out["total"] for _, out, _ in done),
+                      "patterns": dict(sorted(pats.items(), key=lambda kv: int(kv[0]))),
+                      "dropped": dropped, "oracle_s_max_root": max((s for _, _, s in done), default=0.0),
+                      "rule": f"up to {RMAT_PER_BAND} seeded roots (seed {60 + k}) per up-degree band "
+                              f"{[b for b, _ in RMAT_BANDS]}, keeping those the oracle's ESU route "
+                              f"finishes within {RMAT_ROOT_LIMIT_S} s"})
+    with open(os.path.join(HERE, "rmat16_strat.json"), "w") as f:
+        json.dump({"workload": "rmat16", "sha256": g.sha256(), "route": "esu", "cases": cases}, f, indent=0)
+    print("rmat16_strat", [(c["k"], len(c["roots"]), len(c["dropped"]), c["total"]) for c in cases], flush=True)
+
+
 def ba_graphs():
     """48 seeded graph indices of the 4,096-graph Barabasi-Albert batch."""
     rng = np.random.default_rng(40)
@@ -346,6 +422,9 @@ SPECS = {
 
 def main(names):
     O.build()
+    if "rmat16_strat" in names:
+        write_rmat16_strat()
+        names = [n for n in names if n != "rmat16_strat"]
     ctx = mp.get_context("spawn")
     if "ba4096" in names:
         with ctx.Pool(os.cpu_count() or 1) as pool:
@@ -379,4 +458,8 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(SPECS) + ["ba4096", "chunglu1m_full", "chunglu1m_k78"] + list(FULL_SPECS))
+    if sys.argv[1:2] == ["--one-root"]:
+        one_root(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]))
+        sys.exit(0)
+    main(sys.argv[1:] or list(SPECS) + ["ba4096", "chunglu1m_full", "chunglu1m_k78", "rmat16_strat"]
+         + list(FULL_SPECS))

@@ -417,3 +417,31 @@ def test_chunglu_range_equals_single_counts():
     h = G.from_edges(keep, e[:, 0], e[:, 1])
     dh = gpm.graph_from_csr(h)
     assert motif_by_code(dh, 3).get(7, 0) == gpm.gpm_clique_count(dh, 3)
+
+
+# ------------------------------------------------------- overflow contract
+
+@pytest.mark.parametrize("blocks,threads,where", [(1, 32, "lane"), (1, 32, "warp"), (1, 64, "block"),
+                                                  (2, 32, "grid")])
+def test_overflow_is_reported_not_wrapped(blocks, threads, where):
+    """The kernels' reduction path (lane adds, warp sum, block counter,
+    global counter) on values whose true sum is 2^64 (must return
+    GPM_EOVERFLOW) and 2^64 - 1 (must return it exactly), with the two large
+    values placed in one lane, two lanes of a warp, two warps of a block or
+    two blocks."""
+    nthreads = blocks * threads
+    j = {"lane": nthreads, "warp": 1, "block": 32, "grid": 32}[where]
+    v = np.zeros(2 * nthreads, dtype=np.uint64)
+    v[0] = np.uint64(1 << 63)
+    v[j] = np.uint64(1 << 63)
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.gpm_selftest_sum(v, blocks, threads)
+    assert e.value.status == gpm.GPM_EOVERFLOW
+    v[j] = np.uint64((1 << 63) - 1)
+    assert gpm.gpm_selftest_sum(v, blocks, threads) == (1 << 64) - 1
+
+
+def test_selftest_sum_matches_python():
+    rng = np.random.default_rng(7)
+    v = rng.integers(0, 1 << 50, size=100_000, dtype=np.uint64)
+    assert gpm.gpm_selftest_sum(v, 37, 96) == int(v.astype(object).sum())
