@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k8", action="store_true", help="skip the timed k = 4..8 enumeration")
     ap.add_argument("--no-configs", action="store_true", help="skip the per-workload entries")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small launch of a kernel (for ncu captures) and exit")
     return ap.parse_args()
 
 
@@ -523,8 +525,44 @@ def k4_8_entry(dg, g, stream) -> dict:
     return res
 
 
+def _profile_case(name: str) -> None:
+    """One launch of a kernel on a case small enough for an ncu capture
+    (inputs larger than L2, a few hundred MB on the device, at most about a
+    second), after one untimed launch of the same call."""
+    import torch
+
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    graph, run = PROFILE_CASES[name]
+    g = G.workload(graph)
+    dg = gpm.graph_from_csr(g, stream=stream)
+    for _ in range(2):
+        out = run(gpm, g, dg)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "result": [int(x) for x in np.ravel(out)][:8], "stats": gpm.gpm_get_stats(dg)}))
+
+
+PROFILE_CASES = {
+    # the headline kernel: every root, k = 4..6 (two-level tail) and the
+    # 1/64 heaviest-first sample at k = 7 (compacted three-level tail)
+    "clique_chunglu1m_k4_6": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_clique_count_range(dg, 4, 6)),
+    "clique_chunglu1m_k7_sample": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_count_roots(
+        dg, gpm.GPM_APP_CLIQUE, 7, heaviest_first(g)[0::64])[0]),
+    # the motif kernel: marks in HBM (R-MAT, one heavy root) and in shared
+    # memory (the block model graph)
+    "motif_rmat16_k5_root132": ("rmat16", lambda gpm, g, dg: gpm.gpm_count_roots(
+        dg, gpm.GPM_APP_MOTIF, 5, np.array([132], dtype=np.int32))[0]),
+    "motif_sbm2000_k5": ("sbm2000", lambda gpm, g, dg: gpm.gpm_motif_count(dg, 5)),
+}
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        _profile_case(args.profile_case)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -173,6 +173,9 @@ typedef struct {
                                /* entry class instead of leaf by leaf (0: never)                     */
     int32_t clique_compact3;   /* three-level clique tail on the node's members whenever that        */
                                /* shortens the rows: 1 (default) or 0                                */
+    int32_t batch_split;       /* batched launch: roots heavier than 1/4096 of the total estimated   */
+                               /* work are cut into this many units over ranges of their children    */
+                               /* before the launch (0 or 1: none; at most 64)                       */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */
@@ -301,12 +304,16 @@ void gpm_batch_destroy(gpm_batch* b);
 gpm_status gpm_batch_count(gpm_batch* b, int clique_k, int motif_k, uint64_t* clique_counts, uint64_t* motif_counts);
 
 /*
- * Autotune the launch shape for (clique_k, motif_k): warps per block {2, 4,
- * 8, 16} x resident blocks per SM {max, 1, 2} x unit order {tasks
- * grouped, merged}, each timed as the median of `reps` replays; the fastest
- * is kept for this batch (and cached in-process for batches of the same
- * shape).  best (nullable) receives it; best_ms (nullable) its median time,
- * or -1 when it came from the cache.
+ * Autotune the launch for (clique_k, motif_k), each candidate timed as the
+ * median of `reps` replays, in three stages: (1) warps per block {2, 4, 8,
+ * 16} x resident blocks per SM {max, 1, 2} x unit order {tasks grouped,
+ * merged}; (2) with the best of those, the motif tail's class-counting
+ * threshold motif_agg_min {0, 4, 16, 64}; (3) the split of heavy roots
+ * batch_split {1, 4, 16}.  The per-warp stack is not a knob: its size is
+ * fixed by the largest degree (a smaller one could not hold the extension
+ * arrays).  The fastest is kept for this batch (and cached in-process for
+ * batches of the same shape).  best (nullable) receives it; best_ms
+ * (nullable) its median time, or -1 when it came from the cache.
  */
 gpm_status gpm_batch_autotune(gpm_batch* b, int clique_k, int motif_k, int reps, gpm_config* best,
                               double* best_ms);
@@ -368,6 +375,17 @@ gpm_status gpm_motif_count_noalloc(const int32_t* indptr, const int32_t* indices
  * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_EOVERFLOW.
  */
 gpm_status gpm_selftest_sum(const uint64_t* values, int64_t n, int32_t blocks, int32_t threads, uint64_t* out);
+
+/*
+ * L2 read bandwidth of the current device in GB/s (not in the paper: the
+ * denominator of the motif kernel's roofline, whose adjacency lists and
+ * per-warp marks live in L2).  A buffer of `bytes` (1 MB .. 96 MB, inside
+ * L2) is read `reps` times after a warm pass: mode 0 with coalesced 16-byte
+ * loads (bytes / time), mode 1 with one 4-byte load per pseudo-random
+ * 32-byte sector (sectors x 32 B / time, the access shape of the marks).
+ * Allocates a temporary buffer.  Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA.
+ */
+gpm_status gpm_measure_l2(int64_t bytes, int32_t mode, int32_t reps, double* gbs);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* gpm_last_error(void);

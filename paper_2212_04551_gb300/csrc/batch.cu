@@ -9,14 +9,16 @@
 //
 // Small graphs keep the whole per-warp motif state in shared memory: marks are
 // indexed by the vertex's offset inside its graph (mbase = graph_off[g]), so
-// a warp needs only (largest graph) bytes of marks.  No unit is split: the
-// units are short, and warps simply leave when the unit counter runs out --
-// no waiting at all.
+// a warp needs only (largest graph) bytes of marks.  Units are split only
+// statically: the heaviest roots can be cut into several child ranges before
+// the launch (batch_split); warps simply leave when the unit counter runs out
+// -- no waiting at all.
 //
 // The launch (counter resets, kernel, read-back) is captured once into a CUDA
 // graph per (clique k, motif k, launch shape) and replayed on every call.  An
-// autotuner times the replay over warps per block, resident blocks per SM
-// and the unit order, and keeps the fastest.
+// autotuner times the replay over warps per block, resident blocks per SM,
+// the unit order, the class-counting threshold of the motif tail and the
+// split of heavy roots, and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,13 +48,14 @@ struct gpm_batch {
     gpm_stats stats{};
     struct Captured {
         cudaGraphExec_t exec = nullptr;
-        gpm::DevBuf units;           // this launch's unit list (baked into the graph)
+        gpm::DevBuf units, uranges;  // this launch's unit list (baked into the graph)
         gpm::DevBuf dev_out;         // [G] clique + [G*npat] motif + Control
         unsigned long long* host_out = nullptr;   // pinned
         size_t words = 0;
         int blocks = 0, wpb = 0;
     };
-    std::map<std::tuple<int, int, int, int, int, int>, Captured> graphs;   // (kc, km, wpb, bps, order, motif_agg_min)
+    // (kc, km, wpb, bps, order, motif_agg_min, batch_split)
+    std::map<std::tuple<int, int, int, int, int, int, int>, Captured> graphs;
 };
 
 namespace gpm {
@@ -67,6 +70,7 @@ struct BatchParams {
     const int32_t* __restrict__ goff;
     const int32_t* __restrict__ vgraph;
     const int32_t* __restrict__ units;    // (task << 31) | root
+    const int32_t* __restrict__ uranges;  // (piece << 16) | pieces: the unit's share of the root's children
     long long n_units;
     int kc, km;                           // clique / motif sizes (0: task absent)
     int npat;
@@ -166,6 +170,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
         const int task = (int)(((unsigned)code) >> 31);
         const int r = code & 0x7fffffff;
         const int gidx = p.vgraph[r];
+        const int piece = p.uranges[u] >> 16, pieces = max(p.uranges[u] & 0xffff, 1);
         if (task == 0) {
             // ---- clique unit
             const int d = p.outdeg[r];
@@ -173,8 +178,8 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
             if (lane == 0) {
                 unit->root_pos = 0;
                 unit->depth = 0;
-                unit->lo = 0;
-                unit->hi = -1;
+                unit->lo = (int)((long long)d * piece / pieces);
+                unit->hi = pieces > 1 ? (int)((long long)d * (piece + 1) / pieces) : -1;
             }
             __syncwarp();
             unsigned long long km1 = 0, wops = 0;
@@ -193,9 +198,10 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
             mt_setup_prefix(mw, W, 1, lane);
             const int lo = mt_root_ext_begin(p.indptr, p.indices, r, lane);
             if (lane == 0) {
-                W->len[1] = p.indptr[r + 1] - lo;
-                W->cur[1] = 0;
-                W->hi[1] = p.indptr[r + 1] - lo;
+                const int len = p.indptr[r + 1] - lo;
+                W->len[1] = len;
+                W->cur[1] = (int)((long long)len * piece / pieces);
+                W->hi[1] = (int)((long long)len * (piece + 1) / pieces);
             }
             __syncwarp();
             unsigned long long leaves = 0, scanned = 0;
@@ -222,7 +228,8 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
 // first), then every clique root (heaviest out-degree first).  Mode 1: both
 // tasks merged into one heaviest-first list (weights: degree for motif units,
 // out-degree for clique units, scaled to a common range).
-static long long build_units(gpm_batch* b, int kc, int km, int mode, gpm::DevBuf& out) {
+static long long build_units(gpm_batch* b, int kc, int km, int mode, int split, gpm::DevBuf& out,
+                             gpm::DevBuf& out_ranges) {
     gpm_graph* g = b->g;
     const int n = g->n;
     std::vector<int32_t> deg(n), od(n);
@@ -245,12 +252,30 @@ static long long build_units(gpm_batch* b, int kc, int km, int mode, gpm::DevBuf
     } else {
         std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
     }
-    std::vector<int32_t> codes(items.size());
-    for (size_t i = 0; i < items.size(); i++) codes[i] = items[i].second;
+    // split: units heavier than 1/4096 of the total weight become `split`
+    // units over equal ranges of the root's children (kept in place: the
+    // order stays heaviest first)
+    double total = 0.0;
+    for (const auto& it : items) total += it.first;
+    const int pieces = std::max(1, std::min(split, 64));
+    std::vector<int32_t> codes, ranges;
+    codes.reserve(items.size());
+    ranges.reserve(items.size());
+    for (const auto& it : items) {
+        const int np = (pieces > 1 && it.first > total / 4096.0) ? pieces : 1;
+        for (int q = 0; q < np; q++) {
+            codes.push_back(it.second);
+            ranges.push_back((q << 16) | np);
+        }
+    }
     out.ensure(sizeof(int32_t) * std::max<size_t>(codes.size(), 1));
-    if (!codes.empty())
+    out_ranges.ensure(sizeof(int32_t) * std::max<size_t>(ranges.size(), 1));
+    if (!codes.empty()) {
         GPM_CUDA(cudaMemcpyAsync(out.ptr, codes.data(), sizeof(int32_t) * codes.size(), cudaMemcpyHostToDevice,
                                  b->stream));
+        GPM_CUDA(cudaMemcpyAsync(out_ranges.ptr, ranges.data(), sizeof(int32_t) * ranges.size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+    }
     GPM_CUDA(cudaStreamSynchronize(b->stream));
     return (long long)codes.size();
 }
@@ -259,13 +284,14 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     gpm_graph* g = b->g;
     const int wpb = b->cfg.warps_per_block > 0 ? b->cfg.warps_per_block : 8;
     const int bps = b->cfg.blocks_per_sm;
-    const auto key = std::make_tuple(kc, km, wpb, bps, b->order_mode, b->cfg.motif_agg_min);
+    const int split = std::max(1, b->cfg.batch_split);
+    const auto key = std::make_tuple(kc, km, wpb, bps, b->order_mode, b->cfg.motif_agg_min, split);
     auto it = b->graphs.find(key);
     if (it != b->graphs.end()) return it->second;
 
     if (kc > 0) ensure_dag(g);
-    DevBuf units;
-    const long long n_units = build_units(b, kc, km, b->order_mode, units);
+    DevBuf units, uranges;
+    const long long n_units = build_units(b, kc, km, b->order_mode, split, units, uranges);
     const int npat = km > 0 ? (int)pattern_table(km).num_patterns : 0;
 
     BatchParams p{};
@@ -278,6 +304,7 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
     p.goff = b->goff.as<int32_t>();
     p.vgraph = b->vgraph.as<int32_t>();
     p.units = units.as<int32_t>();
+    p.uranges = uranges.as<int32_t>();
     p.n_units = n_units;
     p.kc = kc;
     p.km = km;
@@ -311,6 +338,7 @@ static gpm_batch::Captured& capture(gpm_batch* b, int kc, int km) {
 
     gpm_batch::Captured& c = b->graphs[key];
     c.units = std::move(units);
+    c.uranges = std::move(uranges);
     const size_t G = (size_t)b->n_graphs;
     const size_t ctl_words = (sizeof(Control) + 7) / 8;
     c.words = G + G * npat + ctl_words;
@@ -504,30 +532,56 @@ gpm_config batch_autotune(gpm_batch* b, int kc, int km, int reps, double* best_m
     int best_mode = b->order_mode;
     double best_t = 1e300;
     const gpm_config saved = b->cfg;
+    auto trial = [&](const gpm_config& c, int mode) {
+        b->cfg = c;
+        b->order_mode = mode;
+        std::vector<float> t;
+        try {
+            gpm_batch::Captured& cap = capture(b, kc, km);
+            replay(b, cap);   // warm
+            for (int r = 0; r < std::max(1, reps); r++) t.push_back(replay(b, cap));
+        } catch (const Error&) {
+            return;           // shape not launchable (shared memory): skip it
+        }
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (med < best_t) {
+            best_t = med;
+            best = c;
+            best_mode = mode;
+        }
+    };
+    // stage 1: launch shape and unit order
     for (int mode = 0; mode < 2; mode++)
         for (int wpb : {2, 4, 8, 16})
             for (int bps : {0, 1, 2}) {
                 gpm_config c = saved;
                 c.warps_per_block = wpb;
                 c.blocks_per_sm = bps;
-                b->cfg = c;
-                b->order_mode = mode;
-                std::vector<float> t;
-                try {
-                    gpm_batch::Captured& cap = capture(b, kc, km);
-                    replay(b, cap);   // warm
-                    for (int r = 0; r < std::max(1, reps); r++) t.push_back(replay(b, cap));
-                } catch (const Error&) {
-                    continue;   // shape not launchable (shared memory), skip it
-                }
-                std::sort(t.begin(), t.end());
-                const double med = t[t.size() / 2];
-                if (med < best_t) {
-                    best_t = med;
-                    best = c;
-                    best_mode = mode;
-                }
+                trial(c, mode);
             }
+    // stage 2: class-counting threshold of the motif tail (0: leaf by leaf)
+    if (km > 0) {
+        const gpm_config base = best;
+        const int mode = best_mode;
+        for (int agg : {0, 4, 16, 64}) {
+            if (agg == base.motif_agg_min) continue;
+            gpm_config c = base;
+            c.motif_agg_min = agg;
+            trial(c, mode);
+        }
+    }
+    // stage 3: split of the heaviest roots into child ranges
+    {
+        const gpm_config base = best;
+        const int mode = best_mode;
+        for (int split : {1, 4, 16}) {
+            if (split == std::max(1, base.batch_split)) continue;
+            gpm_config c = base;
+            c.batch_split = split;
+            trial(c, mode);
+        }
+    }
     b->cfg = best;
     b->order_mode = best_mode;
     cache[sig] = {best, best_mode};
@@ -539,6 +593,8 @@ void batch_set_config(gpm_batch* b, const gpm_config& c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || (c.warps_per_block & (c.warps_per_block - 1)))
         fail(GPM_EINVAL, "warps_per_block must be a power of two in [1, 16]");
     if (c.blocks_per_sm < 0) fail(GPM_EINVAL, "blocks_per_sm < 0");
+    if (c.motif_agg_min < 0) fail(GPM_EINVAL, "motif_agg_min < 0");
+    if (c.batch_split < 0 || c.batch_split > 64) fail(GPM_EINVAL, "batch_split must be in [0, 64]");
     b->cfg = c;
 }
 

@@ -227,6 +227,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.clique_compact < 0 || c.clique_compact > 2) fail(GPM_EINVAL, "clique_compact must be 0, 1 or 2");
         if (c.motif_agg_min < 0) fail(GPM_EINVAL, "motif_agg_min < 0");
         if (c.clique_compact3 != 0 && c.clique_compact3 != 1) fail(GPM_EINVAL, "clique_compact3 must be 0 or 1");
+        if (c.batch_split < 0 || c.batch_split > 64) fail(GPM_EINVAL, "batch_split must be in [0, 64]");
         g->cfg = c;
     });
 }

@@ -383,6 +383,7 @@ gpm_config default_config() {
     c.clique_compact = 0;
     c.motif_agg_min = 16;
     c.clique_compact3 = 1;
+    c.batch_split = 1;
     return c;
 }
 

@@ -46,7 +46,7 @@ class gpm_config(ctypes.Structure):
                 ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
                 ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32),
                 ("clique_compact", ctypes.c_int32), ("motif_agg_min", ctypes.c_int32),
-                ("clique_compact3", ctypes.c_int32)]
+                ("clique_compact3", ctypes.c_int32), ("batch_split", ctypes.c_int32)]
 
 
 class gpm_stats(ctypes.Structure):
@@ -96,6 +96,7 @@ SIGNATURES = {
     "gpm_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
     "gpm_motif_count_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, _u64p, ctypes.c_int64, _vp]),
     "gpm_selftest_sum": (ctypes.c_int, [_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _u64p]),
+    "gpm_measure_l2": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
 }
 GPM_MLP_PARAMS = 4801
 
@@ -429,6 +430,7 @@ def gpm_batch_set_config(b: Batch, **kw) -> None:
     c.donate_after_us = 50
     c.motif_agg_min = 16
     c.clique_compact3 = 1
+    c.batch_split = 1
     for key, val in kw.items():
         setattr(c, key, int(val))
     _check(load().gpm_batch_set_config(b, ctypes.byref(c)), "gpm_batch_set_config")
@@ -474,4 +476,11 @@ def gpm_selftest_sum(values, blocks: int = 1, threads: int = 32) -> int:
     out = ctypes.c_uint64()
     _check(load().gpm_selftest_sum(v.ctypes.data_as(_u64p), int(v.shape[0]), int(blocks), int(threads),
                                    ctypes.byref(out)), "gpm_selftest_sum")
+    return out.value
+
+
+def gpm_measure_l2(nbytes: int = 64 << 20, mode: int = 0, reps: int = 20) -> float:
+    """L2 read bandwidth in GB/s (mode 0 coalesced, mode 1 random 32-byte sectors)."""
+    out = ctypes.c_double()
+    _check(load().gpm_measure_l2(int(nbytes), int(mode), int(reps), ctypes.byref(out)), "gpm_measure_l2")
     return out.value

@@ -59,8 +59,14 @@ def test_batch_single_task_and_shapes(small_batch):
         gpm.gpm_batch_set_config(b, warps_per_block=wpb, blocks_per_sm=bps)
         cc, mc = gpm.gpm_batch_count(b, 4, 5)
         assert np.array_equal(cc, ref_c) and np.array_equal(mc, ref_m), (wpb, bps)
+    # the other tuned knobs: class-counting threshold and heavy-root split
+    for agg, split in [(0, 1), (1, 1), (4, 16), (64, 4), (16, 64)]:
+        gpm.gpm_batch_set_config(b, warps_per_block=4, motif_agg_min=agg, batch_split=split)
+        cc, mc = gpm.gpm_batch_count(b, 4, 5)
+        assert np.array_equal(cc, ref_c) and np.array_equal(mc, ref_m), (agg, split)
     best, ms = gpm.gpm_batch_autotune(b, 4, 5, reps=1)
     assert best["warps_per_block"] in (2, 4, 8, 16)
+    assert best["motif_agg_min"] in (0, 4, 16, 64) and best["batch_split"] in (1, 4, 16)
     cc, mc = gpm.gpm_batch_count(b, 4, 5)
     assert np.array_equal(cc, ref_c) and np.array_equal(mc, ref_m)
 

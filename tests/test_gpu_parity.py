@@ -442,6 +442,64 @@ def test_overflow_is_reported_not_wrapped(blocks, threads, where):
 
 
 def test_selftest_sum_matches_python():
+    """Many values over an odd launch shape: the exact sum when it fits
+    (100,000 values below 2^40), GPM_EOVERFLOW when it does not (below
+    2^50: the true sum is about 5.6e19 > 2^64)."""
     rng = np.random.default_rng(7)
-    v = rng.integers(0, 1 << 50, size=100_000, dtype=np.uint64)
+    v = rng.integers(0, 1 << 40, size=100_000, dtype=np.uint64)
     assert gpm.gpm_selftest_sum(v, 37, 96) == int(v.astype(object).sum())
+    w = rng.integers(0, 1 << 50, size=100_000, dtype=np.uint64)
+    assert int(w.astype(object).sum()) >= 1 << 64
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.gpm_selftest_sum(w, 37, 96)
+    assert e.value.status == gpm.GPM_EOVERFLOW
+
+
+def _chunglu_heaviest_first(g):
+    d = g.degrees()
+    e = g.edges()
+    du, dv = d[e[:, 0]], d[e[:, 1]]
+    fwd = (du < dv) | ((du == dv) & (e[:, 0] < e[:, 1]))
+    outdeg = np.bincount(np.where(fwd, e[:, 0], e[:, 1]), minlength=g.n)
+    return np.argsort(-outdeg, kind="stable").astype(np.int32)
+
+
+def test_chunglu_k7_every_root_matches_oracle():
+    """The benchmark's launch shape at its deepest step size: every root of
+    chunglu1m, heaviest oriented out-degree first, donation on, per-root
+    output.  The 6- and 7-clique counts of every root (hashed, by vertex id)
+    and their totals equal the oracle's bitset route over every root
+    (tests/golden/chunglu1m_k78.json), and one enumeration to depth 7 gives
+    the same totals."""
+    import hashlib
+    data = _golden("chunglu1m_k78")
+    g = G.workload("chunglu1m")
+    assert g.sha256() == data["sha256"]
+    dg = gpm.graph_from_csr(g)
+    order = _chunglu_heaviest_first(g)
+    want = data["k7_all_roots"]
+    for k in (6, 7):
+        c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, k, order, per_root=True)
+        assert int(c[0]) == want["cliques"][str(k)], k
+        by_id = np.zeros(g.n, dtype="<u8")
+        by_id[order] = pr
+        assert hashlib.sha256(by_id.tobytes()).hexdigest() == want["per_root_sha256"][str(k)], k
+    got = [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 7)]
+    assert got == [want["cliques"][str(k)] for k in (4, 5, 6, 7)]
+
+
+def test_chunglu_k8_sample_per_root_matches_oracle():
+    """8-cliques of the stored 1/64 sample of chunglu1m's roots (every 64th
+    root of the heaviest-first order, starting at the heaviest), root by
+    root, against the oracle's bitset route."""
+    data = _golden("chunglu1m_k78")
+    g = G.workload("chunglu1m")
+    dg = gpm.graph_from_csr(g)
+    sample = _chunglu_heaviest_first(g)[0::64]
+    want = {r: (c7, c8) for r, c7, c8 in data["k8_sample"]["per_root"]}
+    c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, 8, sample, per_root=True)
+    assert int(c[0]) == data["k8_sample"]["cliques"]["8"]
+    assert [int(x) for x in pr] == [want.get(int(r), (0, 0))[1] for r in sample]
+    c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, 7, sample, per_root=True)
+    assert int(c[0]) == data["k8_sample"]["cliques"]["7"]
+    assert [int(x) for x in pr] == [want.get(int(r), (0, 0))[0] for r in sample]
