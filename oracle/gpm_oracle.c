@@ -6,8 +6,11 @@
  * the benchmark's CPU-baseline leg may load it; the library never does, and
  * this file shares no code, header or table with the CUDA sources.
  *
- * What it implements (ESU/DAG/bitmap tricks of the GPU path are deliberately
- * absent; every step is the paper's, in the paper's order):
+ * What it implements.  The first routes below follow the paper's steps in
+ * the paper's order; the later ones are faster restatements of the same
+ * definitions, each pinned against the first ones and against closed forms
+ * (tests/test_oracle_pins.py), and used only where the paper-order routes
+ * cannot finish a full-size stored value:
  *
  *  - Eq. 1 (enumeration function E(G,tr,k)): a traversal tr grows by one
  *    vertex from its extensions while |tr| < k and is handed to the output
@@ -30,7 +33,14 @@
  *  - Brute force over all k-subsets for tiny graphs (n <= 40), classifying
  *    every induced subgraph, disconnected ones included.
  *  - Instrumentation of the clique search tree (nodes per clique size and
- *    the bytes a sorted-list merge would move, B_alg).
+ *    the bytes a sorted-list merge would move, B_alg), on the (degree, id)
+ *    orientation with sorted-list merges.
+ *  - Motif counts by Wernicke's ESU enumeration (exclusive extension, every
+ *    connected k-set once from its smallest vertex), classified by the same
+ *    canonical code.
+ *  - Clique counts of every size on bitsets over each root's
+ *    out-neighbourhood (the same orientation; candidates as bitsets instead
+ *    of sorted lists).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *  - filter polarity: Algorithm 3 writes "if P then invalidate" while the

@@ -362,6 +362,22 @@ def test_rmat16_full_size_identities():
     assert lhs == sum(comb(int(x), 3) for x in d)
 
 
+def test_rmat16_k5_every_root_star_identity():
+    """5-vertex motifs over every root of R-MAT scale 16 -- the hub (degree
+    6,444, id 0) roots about 7.6e13 of them -- in the benchmark's launch
+    shape: sum_p dom(p) count_p = sum_v C(d(v), 4), with dom(p) the number of
+    vertices of pattern p adjacent to all the others (every 5-set with a
+    spanning star is connected, and is counted once per star centre); and
+    the per-root totals add up to the pattern totals."""
+    g = G.workload("rmat16")
+    dg = gpm.graph_from_csr(g)
+    d = g.degrees()
+    c5, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_MOTIF, 5, None, per_root=True)
+    lhs = sum(_dominating(5, gpm.gpm_motif_pattern(5, p)) * int(c) for p, c in enumerate(c5))
+    assert lhs == sum(comb(int(x), 4) for x in d)
+    assert sum(int(x) for x in pr) == sum(int(x) for x in c5)
+
+
 def test_chunglu_full_counts_match_oracle():
     """The benchmark's workload and call at full size: one enumeration to
     depth 6 over every root of chunglu1m (gpm_clique_count_range) gives the
