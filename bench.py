@@ -315,6 +315,7 @@ class Learned:
                  "untrained": L.predict(self.untrained, feats, self.stream)}
         n_roots = g.n if roots is None else len(roots)
         out, ref, sizes = {}, None, None
+        warps = 4864
         for donate in ((1, 0) if static else (1,)):
             gpm.gpm_set_config(dg, donate=donate)
             tag = "donation" if donate else "static"
@@ -324,7 +325,7 @@ class Learned:
                     gpm.gpm_sched_from_scores(dg, gpm.GPM_APP_MOTIF, None, roots, 0, 0)
                     plan = {"split_roots": 0, "chunks": 0}
                 else:
-                    plan = L.schedule(dg, gpm.GPM_APP_MOTIF, preds[name], roots, warps=4864, chunks=8)
+                    plan = L.schedule(dg, gpm.GPM_APP_MOTIF, preds[name], roots, warps=warps)
                 times = []
                 for _ in range(reps):
                     (c, pr), ms = timed(lambda: gpm.gpm_count_scheduled(dg, gpm.GPM_APP_MOTIF, k, n_roots=n_roots,
@@ -335,6 +336,8 @@ class Learned:
                 assert np.array_equal(c, ref), f"{name} schedule changed the counts"
                 ms = statistics.median(times)
                 res[name] = {"ms": ms, "subgraphs_per_s": int(ref.sum()) / (ms / 1000.0), **motif_stats(dg), **plan}
+                if name == "plain":
+                    warps = res[name]["grid"][0] * res[name]["grid"][1]
             if "plain" in res and "learned" in res:
                 res["speedup_learned_vs_plain"] = res["plain"]["ms"] / res["learned"]["ms"]
             if "plain" in res and "untrained" in res:

@@ -252,11 +252,24 @@ gpm_status gpm_mlp_adam(float* master, float* m, float* v, const float* grad, in
  * vertex ids; NULL = every vertex) are ordered by score descending (scores:
  * device pointer to one FP32 per VERTEX; NULL = the plain order: degree for
  * motifs, oriented out-degree for cliques), and the first split_roots of that
- * order are each pre-split into split_chunks units over equal ranges of their
- * children.  Replaces any earlier schedule of that app.
+ * order are each pre-split into split_chunks units over ranges of their
+ * children cut to balance estimated work (a root's child at position c of L
+ * has about L - c candidates after it, so the work from c on is taken to
+ * grow like (L - c)^(k-1)).  Replaces any earlier schedule of that app.
  */
 gpm_status gpm_sched_from_scores(gpm_graph* g, int app, const float* scores, const int32_t* roots,
                                  int64_t n_roots, int32_t split_roots, int32_t split_chunks);
+
+/*
+ * As gpm_sched_from_scores, with each root pre-split in proportion to its
+ * predicted size: scores (required) are read as log1p of each root's
+ * subtree size, the fair share is (sum of the listed roots' sizes) /
+ * target_units, and a root becomes ceil(size / share) units (1 .. max_chunks,
+ * at most 65,536 units in all), cut as above.  target_units is typically a
+ * few times the warps of the launch.
+ */
+gpm_status gpm_sched_balanced(gpm_graph* g, int app, const float* scores, const int32_t* roots, int64_t n_roots,
+                              int64_t target_units, int32_t max_chunks);
 
 /*
  * Exact counts over the scheduled root set of app (as gpm_count_roots, but

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -74,6 +75,98 @@ static const int32_t* custom_or_null(gpm_graph* g, int64_t* n_roots) {
         return ensure_id_order(g);
     }
     return nullptr;   // heaviest-first order, chosen per application
+}
+
+// The schedule of app over a root list: roots ordered by score descending
+// (the plain order when scores is NULL), then the roots chosen by
+// `chunks_of` (score-ordered position, score -> units; 1 = not split) moved to
+// the kernel list's end with their unit counts.
+template <class ChunksOf>
+static void build_schedule(gpm_graph* g, int app, const float* scores, const int32_t* roots, int64_t n_roots,
+                           ChunksOf chunks_of, bool uniform, int32_t uniform_chunks) {
+    if (app != GPM_APP_CLIQUE && app != GPM_APP_MOTIF) fail(GPM_EINVAL, "unknown app");
+    const int64_t nr = roots ? n_roots : g->n;
+    if (nr < 0) fail(GPM_EINVAL, "n_roots < 0");
+    // the caller's list (validated: ids in range, each once)
+    std::vector<int32_t> list(nr);
+    if (roots) {
+        std::vector<uint8_t> seen(g->n, 0);
+        for (int64_t i = 0; i < nr; i++) {
+            const int32_t r = roots[i];
+            if (r < 0 || r >= g->n) fail(GPM_EINVAL, "root id out of range");
+            if (seen[r]) fail(GPM_EINVAL, "root listed twice");
+            seen[r] = 1;
+            list[i] = r;
+        }
+    } else {
+        for (int64_t i = 0; i < nr; i++) list[i] = (int32_t)i;
+    }
+    DevBuf d_list, d_key;
+    d_list.ensure(sizeof(int32_t) * std::max<int64_t>(nr, 1));
+    if (nr > 0)
+        GPM_CUDA(cudaMemcpyAsync(d_list.ptr, list.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, g->stream));
+    const float* key = scores;
+    if (!key) {
+        // plain order: degree (motif) or oriented out-degree (clique) as the score
+        if (app == GPM_APP_CLIQUE) ensure_dag(g);
+        std::vector<int32_t> dh(g->n);
+        const DevBuf& src = app == GPM_APP_CLIQUE ? g->dag_outdeg : g->degree;
+        if (g->n > 0)
+            GPM_CUDA(cudaMemcpyAsync(dh.data(), src.ptr, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, g->stream));
+        GPM_CUDA(cudaStreamSynchronize(g->stream));
+        std::vector<float> fh(g->n);
+        for (int32_t v = 0; v < g->n; v++) fh[v] = (float)dh[v];
+        d_key.ensure(sizeof(float) * std::max(g->n, 1));
+        if (g->n > 0)
+            GPM_CUDA(cudaMemcpyAsync(d_key.ptr, fh.data(), sizeof(float) * g->n, cudaMemcpyHostToDevice, g->stream));
+        key = d_key.as<float>();
+    }
+    auto& S = g->sched[app];
+    S.ready = false;
+    order_by_score(g, key, d_list.as<int32_t>(), nr, S.roots);
+    std::vector<int32_t> ord(nr);
+    if (nr > 0)
+        GPM_CUDA(cudaMemcpyAsync(ord.data(), S.roots.ptr, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, g->stream));
+    std::vector<float> sc;
+    if (scores && g->n > 0) {
+        sc.resize(g->n);
+        GPM_CUDA(cudaMemcpyAsync(sc.data(), scores, sizeof(float) * g->n, cudaMemcpyDeviceToHost, g->stream));
+    }
+    GPM_CUDA(cudaStreamSynchronize(g->stream));
+    // the kernel takes the split roots from the END of its list (their
+    // relative order kept)
+    std::vector<int32_t> kern, split;
+    std::vector<int32_t> off(1, 0);
+    kern.reserve(nr);
+    for (int64_t i = 0; i < nr; i++) {
+        const int32_t ch = chunks_of(i, sc.empty() ? 0.f : sc[ord[i]]);
+        if (ch > 1) {
+            split.push_back(ord[i]);
+            off.push_back(off.back() + ch);
+        } else {
+            kern.push_back(ord[i]);
+        }
+    }
+    const int64_t ns = (int64_t)split.size();
+    kern.insert(kern.end(), split.begin(), split.end());
+    std::vector<int64_t> where(g->n, -1);
+    for (int64_t i = 0; i < nr; i++) where[list[i]] = i;
+    S.caller_index.assign(nr, 0);
+    for (int64_t i = 0; i < nr; i++) S.caller_index[i] = where[kern[i]];
+    if (nr > 0)
+        GPM_CUDA(cudaMemcpyAsync(S.roots.ptr, kern.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, g->stream));
+    S.n = nr;
+    S.n_counter = nr - ns;
+    S.n_seeds = off.back();
+    S.chunks = uniform && ns > 0 ? uniform_chunks : 0;
+    S.chunk_off.release();
+    if (!uniform && ns > 0) {
+        S.chunk_off.ensure(sizeof(int32_t) * off.size());
+        GPM_CUDA(cudaMemcpyAsync(S.chunk_off.ptr, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice,
+                                 g->stream));
+    }
+    GPM_CUDA(cudaStreamSynchronize(g->stream));
+    S.ready = true;
 }
 
 extern "C" {
@@ -287,69 +380,44 @@ gpm_status gpm_sched_from_scores(gpm_graph* g, int app, const float* scores, con
                                  int64_t n_roots, int32_t split_roots, int32_t split_chunks) {
     return guarded([&] {
         check_graph(g);
-        if (app != GPM_APP_CLIQUE && app != GPM_APP_MOTIF) fail(GPM_EINVAL, "unknown app");
         if (split_roots < 0 || split_chunks < 0) fail(GPM_EINVAL, "negative split");
+        const bool on = split_chunks > 1;
+        build_schedule(g, app, scores, roots, n_roots,
+                       [&](int64_t i, float) { return (on && i < split_roots) ? split_chunks : 1; }, true,
+                       split_chunks);
+    });
+}
+
+gpm_status gpm_sched_balanced(gpm_graph* g, int app, const float* scores, const int32_t* roots, int64_t n_roots,
+                              int64_t target_units, int32_t max_chunks) {
+    return guarded([&] {
+        check_graph(g);
+        if (!scores) fail(GPM_EINVAL, "scores is NULL");
+        if (target_units < 1 || max_chunks < 1 || max_chunks > 4096) fail(GPM_EINVAL, "bad target_units or max_chunks");
+        // predicted sizes of the listed roots (scores are log1p of a size)
         const int64_t nr = roots ? n_roots : g->n;
-        if (nr < 0) fail(GPM_EINVAL, "n_roots < 0");
-        // the caller's list (validated: ids in range, each once)
-        std::vector<int32_t> list(nr);
-        if (roots) {
-            std::vector<uint8_t> seen(g->n, 0);
-            for (int64_t i = 0; i < nr; i++) {
-                const int32_t r = roots[i];
-                if (r < 0 || r >= g->n) fail(GPM_EINVAL, "root id out of range");
-                if (seen[r]) fail(GPM_EINVAL, "root listed twice");
-                seen[r] = 1;
-                list[i] = r;
-            }
-        } else {
-            for (int64_t i = 0; i < nr; i++) list[i] = (int32_t)i;
-        }
-        DevBuf d_list, d_key;
-        d_list.ensure(sizeof(int32_t) * std::max<int64_t>(nr, 1));
-        if (nr > 0)
-            GPM_CUDA(cudaMemcpyAsync(d_list.ptr, list.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, g->stream));
-        const float* key = scores;
-        if (!key) {
-            // plain order: degree (motif) or oriented out-degree (clique) as the score
-            if (app == GPM_APP_CLIQUE) ensure_dag(g);
-            std::vector<int32_t> dh(g->n);
-            const DevBuf& src = app == GPM_APP_CLIQUE ? g->dag_outdeg : g->degree;
-            if (g->n > 0)
-                GPM_CUDA(cudaMemcpyAsync(dh.data(), src.ptr, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, g->stream));
-            GPM_CUDA(cudaStreamSynchronize(g->stream));
-            std::vector<float> fh(g->n);
-            for (int32_t v = 0; v < g->n; v++) fh[v] = (float)dh[v];
-            d_key.ensure(sizeof(float) * std::max(g->n, 1));
-            if (g->n > 0)
-                GPM_CUDA(cudaMemcpyAsync(d_key.ptr, fh.data(), sizeof(float) * g->n, cudaMemcpyHostToDevice, g->stream));
-            key = d_key.as<float>();
-        }
-        auto& S = g->sched[app];
-        S.ready = false;
-        order_by_score(g, key, d_list.as<int32_t>(), nr, S.roots);
-        // the kernel takes the split roots from the END of its list: rotate the
-        // top split_roots to the back (their relative order kept)
-        std::vector<int32_t> ord(nr);
-        if (nr > 0)
-            GPM_CUDA(cudaMemcpyAsync(ord.data(), S.roots.ptr, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, g->stream));
+        std::vector<float> sc(g->n);
+        if (g->n > 0)
+            GPM_CUDA(cudaMemcpyAsync(sc.data(), scores, sizeof(float) * g->n, cudaMemcpyDeviceToHost, g->stream));
         GPM_CUDA(cudaStreamSynchronize(g->stream));
-        const int64_t ns = split_chunks > 1 ? std::min<int64_t>(split_roots, nr) : 0;
-        std::vector<int32_t> kern;
-        kern.reserve(nr);
-        for (int64_t i = ns; i < nr; i++) kern.push_back(ord[i]);
-        for (int64_t i = 0; i < ns; i++) kern.push_back(ord[i]);
-        std::vector<int64_t> where(g->n, -1);
-        for (int64_t i = 0; i < nr; i++) where[list[i]] = i;
-        S.caller_index.assign(nr, 0);
-        for (int64_t i = 0; i < nr; i++) S.caller_index[i] = where[kern[i]];
-        if (nr > 0)
-            GPM_CUDA(cudaMemcpyAsync(S.roots.ptr, kern.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice, g->stream));
-        GPM_CUDA(cudaStreamSynchronize(g->stream));
-        S.n = nr;
-        S.n_counter = nr - ns;
-        S.chunks = ns > 0 ? split_chunks : 0;
-        S.ready = true;
+        auto size_of = [](float s) { return std::expm1(std::min(std::max((double)s, 0.0), 80.0)); };
+        double total = 0.0;
+        for (int64_t i = 0; i < nr; i++) {
+            const int32_t r = roots ? roots[i] : (int32_t)i;
+            if (r >= 0 && r < g->n) total += size_of(sc[r]);
+        }
+        const double share = total / (double)target_units;
+        // at most 65,536 units in all (the seed list's capacity)
+        int64_t budget = 65536;
+        build_schedule(g, app, scores, roots, n_roots,
+                       [&](int64_t, float s) {
+                           if (share <= 0.0) return 1;
+                           int32_t ch = (int32_t)std::min<double>(std::ceil(size_of(s) / share), (double)max_chunks);
+                           ch = (int32_t)std::min<int64_t>(std::max(ch, 1), budget);
+                           if (ch > 1) budget -= ch;
+                           return ch;
+                       },
+                       false, 0);
     });
 }
 
@@ -360,7 +428,11 @@ gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, i
         if (!counts) fail(GPM_EINVAL, "counts is NULL");
         if (app != GPM_APP_CLIQUE && app != GPM_APP_MOTIF) fail(GPM_EINVAL, "unknown app");
         auto& S = g->sched[app];
-        if (!S.ready) fail(GPM_EINVAL, "no schedule set for this app (gpm_sched_from_scores)");
+        if (!S.ready) fail(GPM_EINVAL, "no schedule set for this app (gpm_sched_from_scores / gpm_sched_balanced)");
+        SplitPlan plan;
+        plan.chunks = S.chunks;
+        plan.d_chunk_off = S.chunk_off.ptr ? S.chunk_off.as<int32_t>() : nullptr;
+        plan.n_seeds = S.n_seeds;
         unsigned long long* d_pr = nullptr;
         if (per_root) {
             g->per_root_tmp.ensure(sizeof(unsigned long long) * std::max<int64_t>(S.n, 1));
@@ -371,13 +443,13 @@ gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, i
             if (k < 1 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "k out of range [1, 16]");
             if (counts_len < 1) fail(GPM_EINVAL, "counts_len < 1");
             c.assign(1, 0);
-            run_clique(g, k, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, S.chunks);
+            run_clique(g, k, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, &plan);
         } else {
             if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
             const PatternTable& t = pattern_table(k);
             if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
             c.assign(t.num_patterns, 0);
-            run_motif(g, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, S.chunks);
+            run_motif(g, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, &plan);
         }
         if (per_root && S.n > 0) {
             std::vector<uint64_t> tmp(S.n);

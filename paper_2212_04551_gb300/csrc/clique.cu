@@ -248,21 +248,24 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
 }
 
 // Pre-split seeds: split root j (entries [n_counter, n_counter + n_split) of
-// the root list) into `chunks` units over equal index ranges of its children,
-// written to seeds[j*chunks .. (j+1)*chunks).
+// the root list) becomes its units of the plan (chunk_off, else `chunks`
+// each) over ranges of its children cut by gpm_balanced_cut.
 __global__ void k_clique_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
-                              const int32_t* __restrict__ outdeg, CliqueUnit* seeds) {
+                              const int32_t* __restrict__ chunk_off, int k, const int32_t* __restrict__ outdeg,
+                              CliqueUnit* seeds) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_split) return;
     const long long pos = n_counter + j;
     const int d = outdeg[roots[pos]];
-    for (int c = 0; c < chunks; c++) {
-        const long long slot = (long long)j * chunks + c;
+    const long long base = chunk_off ? chunk_off[j] : (long long)j * chunks;
+    const int ch = chunk_off ? chunk_off[j + 1] - chunk_off[j] : chunks;
+    for (int c = 0; c < ch; c++) {
+        const long long slot = base + c;
         CliqueUnit u;
         u.root_pos = (int32_t)pos;
         u.depth = 0;
-        u.lo = (int)((long long)d * c / chunks);
-        u.hi = (int)((long long)d * (c + 1) / chunks);
+        u.lo = gpm_balanced_cut(d, c, ch, k);
+        u.hi = gpm_balanced_cut(d, c + 1, ch, k);
         for (int z = 0; z < GPM_CLIQUE_MAX_K; z++) u.path[z] = 0;
         seeds[slot] = u;
     }
@@ -284,7 +287,7 @@ __global__ void k_clique_small(const int32_t* __restrict__ outdeg, const int32_t
 }
 
 void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
-                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, int split_chunks) {
+                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, const SplitPlan* plan) {
     if (k_lo < 1 || k_hi > GPM_CLIQUE_MAX_K || k_lo > k_hi) fail(GPM_EINVAL, "bad clique size range");
     ensure_dag(g);
     cudaStream_t s = g->stream;
@@ -295,9 +298,12 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
     }
     if (n_counter < 0 || n_counter > n_roots) n_counter = n_roots;
     const int n_split = (int)(n_roots - n_counter);
-    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > CQ_MAX_SEEDS))
+    const int split_chunks = plan ? plan->chunks : 0;
+    const int32_t* chunk_off = plan ? plan->d_chunk_off : nullptr;
+    const unsigned long long n_seed =
+        n_split <= 0 ? 0ull : (chunk_off ? (unsigned long long)plan->n_seeds : (unsigned long long)n_split * split_chunks);
+    if (n_split > 0 && ((!chunk_off && split_chunks < 1) || n_seed > CQ_MAX_SEEDS))
         fail(GPM_EINVAL, "pre-split schedule has too many units");
-    const unsigned long long n_seed = n_split > 0 ? (unsigned long long)n_split * split_chunks : 0ull;
     g->scratch_small.ensure(sizeof(Control));
     Control* ctl = g->scratch_small.as<Control>();
     Control h{};
@@ -367,7 +373,7 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         GPM_CUDA(cudaMemsetAsync(p.mbox, 0, mbox_bytes, s));
         if (n_split > 0)
             k_clique_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks,
-                                                               p.outdeg, seeds);
+                                                               chunk_off, k_hi, p.outdeg, seeds);
         p.ctl = ctl;
         p.per_root = d_per_root;
         p.donate = g->cfg.donate;

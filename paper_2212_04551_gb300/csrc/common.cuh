@@ -111,7 +111,9 @@ struct gpm_graph {
         bool ready = false;
         gpm::DevBuf roots;                 // kernel order: counter roots, then split roots
         int64_t n = 0, n_counter = 0;
-        int32_t chunks = 0;
+        int32_t chunks = 0;                // units per split root (uniform plan)
+        gpm::DevBuf chunk_off;             // per split root unit offsets (balanced plan), else empty
+        int64_t n_seeds = 0;               // units of the split roots in all
         std::vector<int64_t> caller_index; // kernel position -> index in the caller's list
     } sched[2];
 
@@ -175,16 +177,27 @@ struct PatternTable {
 const PatternTable& pattern_table(int k);  // built once per k, cached
 const uint16_t* device_lut(int k);         // uploaded once per (device, k)
 
+// Pre-split of a schedule's split roots (positions n_counter .. n_roots-1 of
+// the root list): root j becomes units d_chunk_off[j] .. d_chunk_off[j+1]-1
+// (device prefix sums), or `chunks` units each when d_chunk_off is null.
+// The cuts between a root's units balance estimated work (see
+// gpm_balanced_cut).
+struct SplitPlan {
+    int chunks = 0;
+    const int32_t* d_chunk_off = nullptr;
+    int64_t n_seeds = 0;
+};
+
 // clique.cu / motif.cu
 // d_roots[0 .. n_roots): the roots; the first n_counter are handed out one by
-// one, the rest are pre-split into split_chunks queue units each (n_counter
-// < 0: no pre-split).  d_roots == NULL: every vertex, heaviest first.
+// one, the rest are pre-split as `plan` says (n_counter < 0: no pre-split).
+// d_roots == NULL: every vertex, heaviest first.
 void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
                 unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
-                int split_chunks = 0);
+                const SplitPlan* plan = nullptr);
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
-               int split_chunks = 0);
+               const SplitPlan* plan = nullptr);
 
 // sched.cu
 void root_features(gpm_graph* g, int k, float* d_out);
@@ -212,6 +225,19 @@ __device__ __forceinline__ unsigned long long gpm_globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Cut q of `ch` over the L children of a root, 0 = c_0 <= c_1 .. <= c_ch = L,
+// so that the units [c_q, c_{q+1}) carry about equal estimated work: a root's
+// child at position c (ESU array position, or orientation position for
+// cliques) has about (L - c) candidates after it, and its subtree grows like
+// (L - c)^(k-2), so the work after c is about (L - c)^(k-1).
+__device__ __forceinline__ int gpm_balanced_cut(int L, int q, int ch, int k) {
+    if (q <= 0) return 0;
+    if (q >= ch) return L;
+    const float r = powf(1.0f - (float)q / (float)ch, 1.0f / (float)max(k - 1, 1));
+    const int c = L - (int)ceilf((float)L * r);
+    return min(max(c, 0), L);
 }
 
 __device__ __forceinline__ unsigned gpm_lanemask_lt() {

@@ -237,12 +237,13 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     for (int j = threadIdx.x; j < p.npat; j += blockDim.x) gpm_atomic_add_cc(&p.counts[j], bcnt[j], &ctl->overflow);
 }
 
-// Pre-split seeds: root j of [n_counter, n_counter + n_split) is cut into
-// `chunks` units over equal index ranges of its first extension set
-// ({u in N(r): u > r}, a suffix of N(r)).
+// Pre-split seeds: root j of [n_counter, n_counter + n_split) becomes its
+// units of the plan (chunk_off, else `chunks` each) over ranges of its first
+// extension set ({u in N(r): u > r}, a suffix of N(r)) cut by
+// gpm_balanced_cut.
 __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_counter, int n_split, int chunks,
-                             const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
-                             MotifUnit* seeds) {
+                             const int32_t* __restrict__ chunk_off, int k, const int32_t* __restrict__ indptr,
+                             const int32_t* __restrict__ indices, MotifUnit* seeds) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_split) return;
     const long long pos = n_counter + j;
@@ -254,13 +255,15 @@ __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_coun
         if (indices[mid] <= r) lo = mid + 1; else hi = mid;
     }
     const int L = e - lo;
-    for (int c = 0; c < chunks; c++) {
-        const long long slot = (long long)j * chunks + c;
+    const long long base = chunk_off ? chunk_off[j] : (long long)j * chunks;
+    const int ch = chunk_off ? chunk_off[j + 1] - chunk_off[j] : chunks;
+    for (int c = 0; c < ch; c++) {
+        const long long slot = base + c;
         MotifUnit u;
         u.root_pos = (int32_t)pos;
         u.depth = 1;
-        u.lo = (int)((long long)L * c / chunks);
-        u.hi = (int)((long long)L * (c + 1) / chunks);
+        u.lo = gpm_balanced_cut(L, c, ch, k);
+        u.hi = gpm_balanced_cut(L, c + 1, ch, k);
         for (int q = 0; q < MT_MAXK; q++) {
             u.sub[q] = q == 0 ? r : -1;
             u.pos[q] = -1;
@@ -270,7 +273,7 @@ __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_coun
 }
 
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
-               unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, int split_chunks) {
+               unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, const SplitPlan* plan) {
     if (k < 1 || k > MT_MAXK) fail(GPM_ENOTIMPL, "motif size k=" + std::to_string(k) + " not built");
     const PatternTable& tab = pattern_table(k);
     const int npat = (int)tab.num_patterns;
@@ -282,9 +285,12 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     }
     if (n_counter < 0 || n_counter > n_roots) n_counter = n_roots;
     const int n_split = (int)(n_roots - n_counter);
-    if (n_split > 0 && (split_chunks < 1 || (unsigned long long)n_split * split_chunks > MT_MAX_SEEDS))
+    const int split_chunks = plan ? plan->chunks : 0;
+    const int32_t* chunk_off = plan ? plan->d_chunk_off : nullptr;
+    const unsigned long long n_seed =
+        n_split <= 0 ? 0ull : (chunk_off ? (unsigned long long)plan->n_seeds : (unsigned long long)n_split * split_chunks);
+    if (n_split > 0 && ((!chunk_off && split_chunks < 1) || n_seed > MT_MAX_SEEDS))
         fail(GPM_EINVAL, "pre-split schedule has too many units");
-    const unsigned long long n_seed = n_split > 0 ? (unsigned long long)n_split * split_chunks : 0ull;
     gpm_stats st{};
     std::vector<unsigned long long> host(npat, 0);
 
@@ -424,8 +430,8 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     k_queue_init<<<16, 256, 0, s>>>(p.ring_seq, cap);
     if (mbox_bytes) GPM_CUDA(cudaMemsetAsync(p.mbox, 0, mbox_bytes, s));
     if (n_split > 0)
-        k_motif_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks, p.indptr,
-                                                          p.indices, seeds);
+        k_motif_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks, chunk_off, k,
+                                                          p.indptr, p.indices, seeds);
     p.ctl = ctl;
     p.per_root = d_per_root;
     p.donate_min = std::max(2, g->cfg.donate_min);

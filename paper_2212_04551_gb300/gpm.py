@@ -87,6 +87,8 @@ SIGNATURES = {
     "gpm_sched_from_scores": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i32p, ctypes.c_int64, ctypes.c_int32,
                                              ctypes.c_int32]),
     "gpm_count_scheduled": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int64, _u64p]),
+    "gpm_sched_balanced": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i32p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int32]),
     "gpm_batch_create": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]),
     "gpm_batch_destroy": (None, [_vp]),
     "gpm_batch_count": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, _u64p]),
@@ -341,6 +343,18 @@ def gpm_sched_from_scores(g: Graph, app: int, scores=None, roots=None, split_roo
         rp, nr = r.ctypes.data_as(_i32p), int(r.shape[0])
     _check(load().gpm_sched_from_scores(g, int(app), sp, rp, nr, int(split_roots), int(split_chunks)),
            "gpm_sched_from_scores")
+
+
+def gpm_sched_balanced(g: Graph, app: int, scores, roots=None, target_units: int = 16384,
+                       max_chunks: int = 64) -> None:
+    sp = _dev_ptr(scores, "scores")
+    if roots is None:
+        rp, nr = None, 0
+    else:
+        r = np.ascontiguousarray(roots, dtype=np.int32)
+        rp, nr = r.ctypes.data_as(_i32p), int(r.shape[0])
+    _check(load().gpm_sched_balanced(g, int(app), sp, rp, nr, int(target_units), int(max_chunks)),
+           "gpm_sched_balanced")
 
 
 def gpm_count_scheduled(g: Graph, app: int, k: int, n_roots: int | None = None, per_root: bool = False):

@@ -151,14 +151,20 @@ def split_plan(pred_log: np.ndarray, warps: int, chunks: int = 8, max_units: int
     return min(heavy, max_units // max(chunks, 1))
 
 
-def schedule(dg, app: int, pred_vertex, roots=None, warps: int = 4864, chunks: int = 8) -> dict:
-    """Order ``roots`` (None: all) by predicted size and pre-split the heaviest."""
+def schedule(dg, app: int, pred_vertex, roots=None, warps: int = 4864, chunks: int = 8,
+             balanced: bool = True, units_per_warp: int = 4, max_chunks: int = 64) -> dict:
+    """Order ``roots`` (None: all) by predicted size and pre-split the
+    heaviest: in proportion to the predicted size (``balanced``: about
+    ``units_per_warp`` units per warp in all, at most ``max_chunks`` per
+    root), or the top few into ``chunks`` units each."""
+    if balanced:
+        gpm.gpm_sched_balanced(dg, app, pred_vertex.contiguous(), roots, units_per_warp * warps, max_chunks)
+        return {"plan": "balanced", "target_units": units_per_warp * warps, "max_chunks": max_chunks}
     pv = pred_vertex.detach().float().cpu().numpy()
     sel = pv if roots is None else pv[np.asarray(roots)]
     n_split = split_plan(sel, warps, chunks)
     gpm.gpm_sched_from_scores(dg, app, pred_vertex.contiguous(), roots, n_split, chunks if n_split else 0)
-    return {"split_roots": n_split, "chunks": chunks if n_split else 0}
-
+    return {"plan": "top", "split_roots": n_split, "chunks": chunks if n_split else 0}
 
 def save(model: Model, path: str, record: dict) -> None:
     """FP32 master weights (little-endian, base64) and the training record."""

@@ -160,6 +160,14 @@ def test_schedules_never_change_counts(torch, app):
         c, pr = gpm.gpm_count_scheduled(dg, app, k, n_roots=len(roots), per_root=True)
         assert np.array_equal(c, ref), (ns, ch)
         assert np.array_equal(pr, ref_pr), (ns, ch)
+    # pre-splits in proportion to the prediction, coarse to very fine (many
+    # empty units: roots with fewer children than units)
+    big = torch.from_numpy(rng.random(g.n).astype(np.float32) * 30).cuda()
+    for scores, target, maxc in [(pred, 64, 4), (pred, 4096, 64), (big, 60000, 4096), (-pred, 500, 16)]:
+        gpm.gpm_sched_balanced(dg, app, scores, roots, target, maxc)
+        c, pr = gpm.gpm_count_scheduled(dg, app, k, n_roots=len(roots), per_root=True)
+        assert np.array_equal(c, ref), (target, maxc)
+        assert np.array_equal(pr, ref_pr), (target, maxc)
     # the whole vertex set, pre-split heavy roots, against the oracle
     gpm.gpm_sched_from_scores(dg, app, pred, None, 40, 16)
     c, _ = gpm.gpm_count_scheduled(dg, app, 3)
