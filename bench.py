@@ -272,6 +272,36 @@ def motif_stats(dg) -> dict:
             "grid": [int(st["grid_blocks"]), int(st["warps_per_block"])]}
 
 
+_L2 = {}
+
+
+def l2_peaks() -> dict:
+    """The GB300's L2 read bandwidth, measured here by the library
+    (gpm_measure_l2): 64 MB streamed with coalesced 16-byte loads, and the
+    same buffer read one 32-byte sector at a time at random."""
+    from paper_2212_04551_gb300 import gpm
+    if not _L2:
+        _L2["stream_gbs"] = max(gpm.gpm_measure_l2(64 << 20, 0, 20) for _ in range(3))
+        _L2["sector_gbs"] = max(gpm.gpm_measure_l2(64 << 20, 1, 20) for _ in range(3))
+    return dict(_L2)
+
+
+def motif_roofline(arm: dict) -> dict:
+    """The motif kernel against L2: every scanned adjacency entry moves 4 B
+    of index (coalesced) and selects one mark byte at a random place, which
+    costs one 32-byte L2 sector; achieved = entries x 36 B / kernel time,
+    against the measured random-sector L2 bandwidth.  (Algorithmic bytes, 4
+    + 1 per entry, are given beside it.)"""
+    pk = l2_peaks()
+    s = arm["kernel_ms"] / 1000.0
+    e = float(arm["adjacency_entries"])
+    ach = e * 36.0 / s / 1e9
+    return {"bound": "l2", "kernel": "k_motif", "achieved": ach, "peak": pk["sector_gbs"], "unit": "GB/s",
+            "frac": ach / pk["sector_gbs"], "peak_kind": "measured random 32-byte sector reads (gpm_measure_l2)",
+            "bytes_per_entry": 36, "algorithmic_gbs": e * 5.0 / s / 1e9,
+            "l2_stream_peak_gbs": pk["stream_gbs"], "units_per_launch": e}
+
+
 # ---------------------------------------------------------- learned scheduler
 
 class Learned:
@@ -398,7 +428,8 @@ def config_rmat16(stream, learned: Learned) -> dict:
     cmp5, c5, _ = learned.compare(dg, g, 5, None, reps=1, arms=("plain", "learned"))
     lhs = sum(dominating(5, gpm.gpm_motif_pattern(5, p)) * int(x) for p, x in enumerate(c5))
     res["k5_all_roots"] = {"subgraphs": int(c5.sum()), **cmp5,
-                           "star_identity": lhs == sum(comb(int(x), 4) for x in d)}
+                           "star_identity": lhs == sum(comb(int(x), 4) for x in d),
+                           "roofline": motif_roofline(cmp5["donation"]["plain"])}
     gs = golden("rmat16_strat")
     if gs is not None and gs["sha256"] == g.sha256():
         for case in gs["cases"]:
@@ -497,7 +528,8 @@ def config_sbm2000(stream, learned: Learned) -> dict:
     cmp6, c6, _ = learned.compare(dg, g, 6, None, reps=1, arms=("plain", "learned", "untrained"))
     gf = golden("sbm2000_full")
     want6 = next((cs["patterns"] for cs in gf["cases"] if cs["k"] == 6 and cs["roots"] is None), None) if gf else None
-    res["motif6"] = {"subgraphs": int(c6.sum()), **cmp6, "oracle_parity": by_code(6, c6) == want6 if want6 else None}
+    res["motif6"] = {"subgraphs": int(c6.sum()), **cmp6, "oracle_parity": by_code(6, c6) == want6 if want6 else None,
+                     "roofline": motif_roofline(cmp6["donation"]["plain"])}
     dg.close()
     return res
 
@@ -553,6 +585,11 @@ PROFILE_CASES = {
     "clique_chunglu1m_k4_6": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_clique_count_range(dg, 4, 6)),
     "clique_chunglu1m_k7_sample": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_count_roots(
         dg, gpm.GPM_APP_CLIQUE, 7, heaviest_first(g)[0::64])[0]),
+    # the bulk of the k = 7 search without its few heaviest roots (whose
+    # split-up tails dominate a small sample): every 16th root from the
+    # 1,024th heaviest on
+    "clique_chunglu1m_k7_bulk": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_count_roots(
+        dg, gpm.GPM_APP_CLIQUE, 7, heaviest_first(g)[1024::16])[0]),
     # the motif kernel: marks in HBM (R-MAT, one heavy root) and in shared
     # memory (the block model graph)
     "motif_rmat16_k5_root132": ("rmat16", lambda gpm, g, dg: gpm.gpm_count_roots(

@@ -34,6 +34,7 @@ constexpr int CQ_MAX_OUTDEG = 1024;          // bitmap rows of at most 32 words
 constexpr int CQ_PAIR_FLUSH = 128;            // run the pair batch once it holds this many
 constexpr int CQ_CW = 5;                      // compacted tail: at most 32 * CQ_CW members
 constexpr int CQ_COMPACT_MIN = 48;            // ... and (clique_compact = 1) at least this many
+constexpr unsigned long long CQ_CHECK_NS = 4000;   // busy warps look for idle ones at most this often
 
 struct CliqueUnit {
     int32_t root_pos;                   // index into the root list
@@ -614,6 +615,56 @@ __device__ __forceinline__ void cq_tail3c_dispatch(const uint32_t* C, const TriR
     else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
 }
 
+// Split point of a node's remaining children (set bits of C in [from, to))
+// for a hand-off: child i has c_i = |C & row_i| candidates and a subtree that
+// grows like c_i^e (e = the levels below it), so the donated suffix [mid, to)
+// is cut where it carries about half of the estimated work; at least one
+// child stays and one goes.  Returns -1 when fewer than two remain.
+// Warp-uniform; two lane-parallel passes over the children.
+__device__ __noinline__ static int cq_balanced_mid(const uint32_t* C, const TriRows& rows, int w, int from, int to,
+                                                   int e, int lane) {
+    float total = 0.f;
+    int n = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        float run = 0.f;
+        int seen = 0;
+        for (int q = 0; q < w; q++) {
+            const uint32_t word = C[q] & range_mask(q, from, to);
+            const bool bit = (word >> lane) & 1u;
+            float wt = 0.f;
+            if (bit) {
+                const int p = 32 * q + lane;
+                const uint32_t* rp = rows.row(p);
+                int c = 0;
+                for (int z = q; z < w; z++) c += __popc(C[z] & rp[z]);
+                wt = __powf((float)c + 1.f, (float)e);
+            }
+            // inclusive prefix of the weights over the lanes of this word
+            float incl = wt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(GPM_FULL_MASK, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned bal = __ballot_sync(GPM_FULL_MASK, bit);
+            if (pass == 1) {
+                // first child whose prefix passes half the total (never the first child)
+                const int rank = seen + __popc(bal & gpm_lanemask_lt());
+                const bool cut = bit && rank >= 1 && run + incl > 0.5f * total;
+                const unsigned cuts = __ballot_sync(GPM_FULL_MASK, cut);
+                if (cuts) return 32 * q + __ffs(cuts) - 1;
+            }
+            run += __shfl_sync(GPM_FULL_MASK, incl, 31);
+            seen += __popc(bal);
+        }
+        if (pass == 0) {
+            total = run;
+            n = seen;
+            if (n < 2) return -1;
+        }
+    }
+    return -1;
+}
+
 // Walk one unit (root r = roots[root_pos], d = |N+(r)|).  Returns false if it
 // stopped on a device error.  Lane-private results: unit_sum (k_hi-cliques)
 // and km1 (k_hi-1 cliques, used when k_lo < k_hi); smaller sizes go to wcnt.
@@ -658,7 +709,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
     const int tail = three ? K - 4 : (K >= 4 ? K - 3 : 1);
     const unsigned long long t_start = DONATE ? gpm_globaltimer() : 0ull;
 
-    int iter = 0;
+    unsigned long long last_check = t_start;   // lane 0
     for (;;) {
         const uint32_t* Cs = cand + s * a.wmax;
         if (s == tail && three) {
@@ -745,14 +796,27 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         __syncwarp();
         if (down) s++;
 
-        if (DONATE && (++iter & 15) == 0) {
+        // look for idle warps after every step, but at most once per
+        // CQ_CHECK_NS: a step can be a whole tail node (milliseconds on a
+        // dense core), so a count of steps would leave idle warps waiting
+        int chk = 0;
+        unsigned long long now = 0;
+        if (DONATE && lane == 0) {
+            now = gpm_globaltimer();
+            if (now - last_check >= CQ_CHECK_NS) {
+                last_check = now;
+                chk = 1;
+            }
+        }
+        if (DONATE) chk = __shfl_sync(GPM_FULL_MASK, chk, 0);
+        if (DONATE && chk) {
             Control* ctl = a.ctl;
             // abort on a device error; split when someone is idle and this
             // unit has already run for a while
             int err = 0, want = 0;
             if (lane == 0) {
                 err = *(volatile int*)&ctl->error;
-                if (gpm_globaltimer() - t_start > a.donate_after_ns) {
+                if (now - t_start > a.donate_after_ns) {
                     const unsigned long long qh = *(volatile unsigned long long*)&ctl->q_head;
                     const unsigned long long qt = *(volatile unsigned long long*)&ctl->q_tail;
                     want = qt > qh;   // a registered idle warp is waiting
@@ -768,19 +832,9 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                     const int from = cur[t], to = hiv[t];
                     const int rem = count_range(Ct, w, from, to, lane);
                     if (rem < max(a.donate_min, 2)) continue;
-                    // keep the first rem - rem/2 remaining children, donate the rest
-                    const int keep = rem - rem / 2;
-                    int seen = 0, mid = -1;
-                    for (int q = 0; q < w && mid < 0; q++) {
-                        const uint32_t word = Ct[q] & range_mask(q, from, to);
-                        const int pc = __popc(word);
-                        if (seen + pc > keep) {
-                            uint32_t wv = word;
-                            for (int z = 0; z < keep - seen; z++) wv &= wv - 1u;
-                            mid = 32 * q + __ffs(wv) - 1;
-                        }
-                        seen += pc;
-                    }
+                    // keep the heavier first children, donate a suffix with
+                    // about half of the estimated work
+                    const int mid = cq_balanced_mid(Ct, rows, w, from, to, max(K - t - 2, 1), lane);
                     if (mid < 0) break;
                     if (lane == 0) {
                         int wid;

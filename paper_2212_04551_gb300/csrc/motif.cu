@@ -359,10 +359,13 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     const bool smem_state =
         warp_state <= 12 * 1024 && fixed_smem + 8 * (sizeof(MtWarp) + agg_bytes + warp_state) <= 200 * 1024;
     const size_t per_warp = sizeof(MtWarp) + agg_bytes + (smem_state ? (size_t)p.smem_warp_bytes : 0);
-    // Marks in HBM (large graphs): every warp owns n mark bytes.  The grid
-    // fills the SMs (the class-counted last levels are latency-bound and want
-    // every resident warp: rmat16 k = 4, 186 ms at 4,864 warps against 317 ms
-    // at 1,216), up to 8 GB of marks in all.
+    // Marks in HBM (large graphs): every warp owns n mark bytes that the
+    // class-counted last levels read at random.  Those loads are
+    // latency-bound, so more warps help, until the marks spill from L2 to
+    // DRAM: the grid holds about 256 MB of marks (never fewer than 8 warps
+    // per SM).  Measured on rmat16 (n = 65,536): 1,216 / 2,432 / 3,648 /
+    // 4,864 warps: 4-motifs 252 / 188 / 175 / 216 ms, 5-motifs of root 132
+    // 541 / 385 / 332 / 354 ms.
     int wpb = g->cfg.warps_per_block > 0
                   ? g->cfg.warps_per_block
                   : best_warps_per_block(smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>,
@@ -373,7 +376,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     // 17.9 s at 4 warps per block, 21.5 s at 16).
     if (smem_state && g->cfg.warps_per_block <= 0) wpb = std::min(wpb, 4);
     if (!smem_state && g->cfg.warps_per_block <= 0 && g->cfg.blocks_per_sm <= 0) {
-        const long long mark_warps = (8ll << 30) / std::max<long long>(g->n, 1);
+        const long long mark_warps = (256ll << 20) / std::max<long long>(g->n, 1);
         const long long per_sm_warps = std::max<long long>(8, mark_warps / std::max(g->num_sms, 1));
         wpb = 4;
         max_per_sm = (int)std::max<long long>(2, per_sm_warps / wpb);
