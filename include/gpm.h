@@ -61,7 +61,7 @@ typedef struct gpm_graph gpm_graph; /* opaque, library-owned */
 
 /* limits */
 #define GPM_CLIQUE_MAX_K 16
-#define GPM_MOTIF_MAX_K  7
+#define GPM_MOTIF_MAX_K  8
 
 /*
  * Copy an undirected CSR graph (Section 2; adjacency lists contiguous, as in
@@ -110,7 +110,9 @@ gpm_status gpm_clique_count_range(gpm_graph* g, int k_lo, int k_hi, uint64_t* co
  * motif counting; aggregate_pattern, Section 4.3.4), 1 <= k <=
  * GPM_MOTIF_MAX_K.  counts: host array of counts_len uint64, counts_len >=
  * gpm_motif_num_patterns(k); entry p is the number of subgraphs whose
- * canonical representative is pattern id p (see gpm_motif_pattern).
+ * canonical representative is pattern id p (see gpm_motif_pattern).  For
+ * k <= 7 the last two levels are counted by entry class (motif_agg_min);
+ * k = 8 counts leaf by leaf into global pattern counters.
  * Errors: GPM_EINVAL (also counts_len too small), GPM_ENOMEM, GPM_ECUDA,
  * GPM_ETIMEOUT, GPM_EOVERFLOW.
  */
@@ -118,7 +120,9 @@ gpm_status gpm_motif_count(gpm_graph* g, int k, uint64_t* counts, int64_t counts
 
 /*
  * Number of connected k-vertex patterns (pattern ids are 0 .. *out - 1):
- * 1, 1, 2, 6, 21, 112, 853 for k = 1 .. 7.
+ * 1, 1, 2, 6, 21, 112, 853, 11117 for k = 1 .. 8.  The k = 8 dictionary is
+ * built on first use (about ten seconds of host time, 512 MB of host memory
+ * while it runs; the table is 256 MB, on the host and on each device).
  */
 gpm_status gpm_motif_num_patterns(int k, int64_t* out);
 

@@ -489,7 +489,7 @@ void destroy_batch(gpm_batch* b) {
 
 void batch_count(gpm_batch* b, int kc, int km, uint64_t* clique_counts, uint64_t* motif_counts) {
     if (kc < 0 || kc > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "clique k out of range [0, 16]");
-    if (km < 0 || km > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "motif k out of range [0, 7]");
+    if (km < 0 || km > 7) fail(GPM_EINVAL, "batched motif k out of range [0, 7] (k = 8 needs global counters)");
     if (kc > 0 && kc < 3) fail(GPM_EINVAL, "batched clique counting needs k >= 3");
     if (km > 0 && km < 3) fail(GPM_EINVAL, "batched motif counting needs k >= 3");
     if (kc > 0 && !clique_counts) fail(GPM_EINVAL, "clique_counts is NULL");

@@ -226,7 +226,7 @@ gpm_status gpm_motif_count(gpm_graph* g, int k, uint64_t* counts, int64_t counts
     return guarded([&] {
         check_graph(g);
         if (!counts) fail(GPM_EINVAL, "counts is NULL");
-        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 8]");
         const PatternTable& t = pattern_table(k);
         if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
         int64_t nr = 0;
@@ -240,7 +240,7 @@ gpm_status gpm_motif_count(gpm_graph* g, int k, uint64_t* counts, int64_t counts
 gpm_status gpm_motif_num_patterns(int k, int64_t* out) {
     return guarded([&] {
         if (!out) fail(GPM_EINVAL, "out is NULL");
-        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 8]");
         *out = pattern_table(k).num_patterns;
     });
 }
@@ -248,7 +248,7 @@ gpm_status gpm_motif_num_patterns(int k, int64_t* out) {
 gpm_status gpm_motif_pattern(int k, int64_t id, uint64_t* adj_code) {
     return guarded([&] {
         if (!adj_code) fail(GPM_EINVAL, "adj_code is NULL");
-        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+        if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 8]");
         const PatternTable& t = pattern_table(k);
         if (id < 0 || id >= t.num_patterns) fail(GPM_EINVAL, "pattern id out of range");
         *adj_code = t.pattern_code[(size_t)id];
@@ -281,7 +281,7 @@ gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, i
             c.assign(1, 0);
             run_clique(g, k, k, d_roots, nr, d_pr, c.data());
         } else {
-            if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+            if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 8]");
             const PatternTable& t = pattern_table(k);
             if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
             c.assign(t.num_patterns, 0);
@@ -445,7 +445,7 @@ gpm_status gpm_count_scheduled(gpm_graph* g, int app, int k, uint64_t* counts, i
             c.assign(1, 0);
             run_clique(g, k, k, S.roots.as<int32_t>(), S.n, d_pr, c.data(), S.n_counter, &plan);
         } else {
-            if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 7]");
+            if (k < 1 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [1, 8]");
             const PatternTable& t = pattern_table(k);
             if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
             c.assign(t.num_patterns, 0);

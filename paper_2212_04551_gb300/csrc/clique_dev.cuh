@@ -710,6 +710,8 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
     const unsigned long long t_start = DONATE ? gpm_globaltimer() : 0ull;
 
     unsigned long long last_check = t_start;   // lane 0
+    int iter = 0;
+    bool big = false;                          // the last step ran a three-level tail node
     for (;;) {
         const uint32_t* Cs = cand + s * a.wmax;
         if (s == tail && three) {
@@ -729,6 +731,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
             __syncwarp();
             if (s == s_base) break;
             s--;
+            big = true;
             continue;
         }
         if (s == tail && K >= 4 && w >= 3 && a.compact != 0) {
@@ -796,19 +799,22 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         __syncwarp();
         if (down) s++;
 
-        // look for idle warps after every step, but at most once per
-        // CQ_CHECK_NS: a step can be a whole tail node (milliseconds on a
-        // dense core), so a count of steps would leave idle warps waiting
+        // look for idle warps after every three-level tail node (one can run
+        // for milliseconds on a dense core) and every 16th other step, but
+        // at most once per CQ_CHECK_NS
         int chk = 0;
         unsigned long long now = 0;
-        if (DONATE && lane == 0) {
-            now = gpm_globaltimer();
-            if (now - last_check >= CQ_CHECK_NS) {
-                last_check = now;
-                chk = 1;
+        if (DONATE && (big || (++iter & 15) == 0)) {
+            big = false;
+            if (lane == 0) {
+                now = gpm_globaltimer();
+                if (now - last_check >= CQ_CHECK_NS) {
+                    last_check = now;
+                    chk = 1;
+                }
             }
+            chk = __shfl_sync(GPM_FULL_MASK, chk, 0);
         }
-        if (DONATE) chk = __shfl_sync(GPM_FULL_MASK, chk, 0);
         if (DONATE && chk) {
             Control* ctl = a.ctl;
             // abort on a device error; split when someone is idle and this

@@ -16,7 +16,10 @@
 //      code (t << 1) | 1; LUT[t] = id of that code's class, or 0xFFFF when
 //      some v_i (i >= 2) has no earlier neighbour (not a traversal).
 //
-// Cost: (#classes) x k! relabellings -- 1044 x 5040 for k = 7.
+// Cost: (#classes) x k! relabellings -- 1044 x 5040 for k = 7, 12,346 x
+// 40,320 for k = 8 (about ten seconds, once per process; the class of every
+// one of the 2^28 full codes is held as 16 bits: 512 MB while it runs, and
+// the k = 8 table itself is 2^27 uint16 = 256 MB).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -76,12 +79,13 @@ static std::unique_ptr<PatternTable> build_table(int k) {
         images.push_back(std::move(img));
     } while (std::next_permutation(perm.begin(), perm.end()));
 
-    const uint32_t UNSET = 0xffffffffu;
-    std::vector<uint32_t> cls(nfull, UNSET);
+    // class ids fit in 16 bits: at most 12,346 classes for k <= 8
+    const uint16_t UNSET = 0xffffu;
+    std::vector<uint16_t> cls(nfull, UNSET);
     std::vector<uint64_t> cls_code;
     for (uint64_t f = 0; f < nfull; f++) {
         if (cls[f] != UNSET) continue;
-        const uint32_t id = (uint32_t)cls_code.size();
+        const uint16_t id = (uint16_t)cls_code.size();
         cls_code.push_back(f);
         for (const auto& img : images) {
             uint64_t r = 0;

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "common.cuh"
 #include "motif_dev.cuh"
@@ -53,7 +54,9 @@ struct MotifParams {
     int agg_words;              // shared words of class counters per warp (mt_agg_words(k))
 };
 
-template <bool SMEM_STATE>
+// GCOUNT: count patterns straight into the global counters (k = 8) instead
+// of per-block shared ones
+template <bool SMEM_STATE, bool GCOUNT>
 __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -63,7 +66,8 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     MtWarp* W = reinterpret_cast<MtWarp*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT) + wib;
     uint32_t* agg = reinterpret_cast<uint32_t*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb) +
                     (size_t)wib * p.agg_words;
-    for (int j = threadIdx.x; j < p.npat; j += blockDim.x) bcnt[j] = 0ull;
+    if (!GCOUNT)
+        for (int j = threadIdx.x; j < p.npat; j += blockDim.x) bcnt[j] = 0ull;
 
     const long long gw = (long long)blockIdx.x * nwb + wib;
     Control* ctl = p.ctl;
@@ -97,7 +101,8 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         a.slab = p.slab + gw * p.slab_ints;
     }
     __syncthreads();
-    BlockSink sink{bcnt, &ctl->overflow};
+    using Sink = typename std::conditional<GCOUNT, GlobalSink, BlockSink>::type;
+    Sink sink{GCOUNT ? p.counts : bcnt, &ctl->overflow};
     const int32_t* __restrict__ indptr = p.indptr;
     const int32_t* __restrict__ indices = p.indices;
 
@@ -234,7 +239,8 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     if (lane == 0) atomicAdd(&ctl->busy_ns, busy);
     if (lane == 0 && scanned) atomicAdd(&ctl->word_ops, scanned);
     __syncthreads();
-    for (int j = threadIdx.x; j < p.npat; j += blockDim.x) gpm_atomic_add_cc(&p.counts[j], bcnt[j], &ctl->overflow);
+    if (!GCOUNT)
+        for (int j = threadIdx.x; j < p.npat; j += blockDim.x) gpm_atomic_add_cc(&p.counts[j], bcnt[j], &ctl->overflow);
 }
 
 // Pre-split seeds: root j of [n_counter, n_counter + n_split) becomes its
@@ -353,7 +359,9 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     const long long warp_state = (long long)p.mark_stride + 4 * p.slab_ints;
     p.smem_warp_bytes = (int)((warp_state + 15) & ~15ll);
     const size_t fixed_smem = sizeof(unsigned long long) * MT_MAXPAT + 16;
-    p.agg_min = g->cfg.motif_agg_min;
+    // the class-counted tail needs two free mark bits at level k-2: k <= 7
+    const bool gcount = npat > MT_MAXPAT;
+    p.agg_min = k <= 7 ? g->cfg.motif_agg_min : 0;
     p.agg_words = p.agg_min > 0 ? mt_agg_words(k) : 0;
     const size_t agg_bytes = sizeof(uint32_t) * (size_t)p.agg_words;
     const bool smem_state =
@@ -368,7 +376,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     // 541 / 385 / 332 / 354 ms.
     int wpb = g->cfg.warps_per_block > 0
                   ? g->cfg.warps_per_block
-                  : best_warps_per_block(smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>,
+                  : best_warps_per_block(smem_state ? (const void*)k_motif<true, false> : (const void*)k_motif<false, false>,
                                          per_warp, fixed_smem);
     int max_per_sm = 0;
     // Marks in shared memory (small graphs): four warps per block share the
@@ -383,7 +391,8 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     }
     const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + (sizeof(MtWarp) + agg_bytes) * wpb + 16;
     const size_t smem = base_smem + (smem_state ? (size_t)wpb * p.smem_warp_bytes : 0);
-    const void* kfun = smem_state ? (const void*)k_motif<true> : (const void*)k_motif<false>;
+    const void* kfun = smem_state ? (gcount ? (const void*)k_motif<true, true> : (const void*)k_motif<true, false>)
+                                  : (gcount ? (const void*)k_motif<false, true> : (const void*)k_motif<false, false>);
     GPM_CUDA(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     Grid gr = plan_grid(g, kfun, wpb, smem, max_per_sm);
     const long long nw = gr.total_warps();
@@ -402,13 +411,13 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
         p.slab = g->scratch_slab.as<int32_t>();
     }
 
-    g->scratch_small.ensure(sizeof(Control) + sizeof(unsigned long long) * MT_MAXPAT);
+    g->scratch_small.ensure(sizeof(Control) + sizeof(unsigned long long) * MT_MAXPAT8);
     Control* ctl = g->scratch_small.as<Control>();
     p.counts = reinterpret_cast<unsigned long long*>(ctl + 1);
     Control h{};
     h.pending = n_counter + (long long)n_seed;
     GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
-    GPM_CUDA(cudaMemsetAsync(p.counts, 0, sizeof(unsigned long long) * MT_MAXPAT, s));
+    GPM_CUDA(cudaMemsetAsync(p.counts, 0, sizeof(unsigned long long) * npat, s));
     if (d_per_root && n_roots > 0)
         GPM_CUDA(cudaMemsetAsync(d_per_root, 0, sizeof(unsigned long long) * n_roots, s));
 
@@ -443,8 +452,13 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
 
     if (n_roots > 0) {
         GPM_CUDA(cudaEventRecord(g->ev0, s));
-        if (smem_state) k_motif<true><<<gr.blocks, wpb * 32, smem, s>>>(p);
-        else k_motif<false><<<gr.blocks, wpb * 32, smem, s>>>(p);
+        if (smem_state) {
+            if (gcount) k_motif<true, true><<<gr.blocks, wpb * 32, smem, s>>>(p);
+            else k_motif<true, false><<<gr.blocks, wpb * 32, smem, s>>>(p);
+        } else {
+            if (gcount) k_motif<false, true><<<gr.blocks, wpb * 32, smem, s>>>(p);
+            else k_motif<false, false><<<gr.blocks, wpb * 32, smem, s>>>(p);
+        }
         GPM_CUDA(cudaGetLastError());
         GPM_CUDA(cudaEventRecord(g->ev1, s));
         st.grid_blocks = gr.blocks;
@@ -545,7 +559,7 @@ static unsigned char* noalloc_scratch_ptr() {
 
 static void motif_count_noalloc(const int32_t* indptr, const int32_t* indices, int32_t n, int k, uint64_t* counts,
                                 int64_t counts_len, cudaStream_t s) {
-    if (k < 3 || k > MT_MAXK) fail(GPM_EINVAL, "k out of range [3, 7] for the allocation-free path");
+    if (k < 3 || k > 7) fail(GPM_EINVAL, "k out of range [3, 7] for the allocation-free path");
     if (n < 0 || n > NA_MAX_N)
         fail(GPM_EINVAL, "n = " + std::to_string(n) + " exceeds the allocation-free limit of " +
                              std::to_string(NA_MAX_N) + " vertices");
@@ -634,13 +648,13 @@ static void motif_count_noalloc(const int32_t* indptr, const int32_t* indices, i
     p.donate = 0;
     p.donate_min = 2;
     p.max_idle_ns = 120000000000ull;
-    GPM_CUDA(cudaFuncSetAttribute(k_motif<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GPM_CUDA(cudaFuncSetAttribute(k_motif<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_motif<true>, wpb * 32, smem));
+    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_motif<true, false>, wpb * 32, smem));
     if (per_sm <= 0) fail(GPM_EINVAL, "kernel cannot be resident");
     if (n > 0) {
         const int grid = std::max(1, std::min(per_sm * sms, (n + wpb - 1) / wpb));
-        k_motif<true><<<grid, wpb * 32, smem, s>>>(p);
+        k_motif<true, false><<<grid, wpb * 32, smem, s>>>(p);
         GPM_CUDA(cudaGetLastError());
     }
     unsigned long long host[MT_MAXPAT];

@@ -31,7 +31,8 @@
 namespace gpm {
 
 constexpr int MT_MAXK = GPM_MOTIF_MAX_K;
-constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns
+constexpr int MT_MAXPAT = 853;                 // connected 7-vertex patterns: per-block shared counters
+constexpr int MT_MAXPAT8 = 11117;              // connected 8-vertex patterns: counted in global memory
 constexpr unsigned long long MT_CHECK_NS = 4000;  // busy warps look for idle ones at most this often
 constexpr float MT_MIN_DONATE_WORK = 2048.f;    // estimated leaves a handed-over range must carry
 constexpr int MT_AGG_UNROLL = 4;                 // adjacency entries per lane per round (mt_tail_agg)
@@ -101,6 +102,14 @@ __device__ __forceinline__ int mt_code_off(int i) { return i * (i - 1) / 2 - 1; 
 // Shared counters of one block (single-graph kernel); ovf: the launch's
 // overflow flag, raised if a counter wraps.
 struct BlockSink {
+    unsigned long long* c;
+    int* ovf;
+    __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }
+};
+
+// The launch's global counters (k = 8: 11,117 patterns do not fit a block's
+// shared memory).
+struct GlobalSink {
     unsigned long long* c;
     int* ovf;
     __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }

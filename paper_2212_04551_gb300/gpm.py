@@ -31,7 +31,7 @@ GPM_ORDER_ID = 0
 GPM_ORDER_DEGREE_DESC = 1
 GPM_ORDER_CUSTOM = 2
 GPM_CLIQUE_MAX_K = 16
-GPM_MOTIF_MAX_K = 7
+GPM_MOTIF_MAX_K = 8
 
 
 class GpmError(RuntimeError):

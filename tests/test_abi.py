@@ -55,7 +55,7 @@ def test_pattern_counts_match_oeis(lib):
         assert gpm.gpm_motif_num_patterns(k) == golden[k]
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_pattern_codes_are_canonical_and_ordered(lib, k):
     """Each id's code is the smallest code of its class (checked with the
     oracle's relabelling-minimum), connected, distinct, and the ids are

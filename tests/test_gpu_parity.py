@@ -519,3 +519,25 @@ def test_chunglu_k8_sample_per_root_matches_oracle():
     c, pr = gpm.gpm_count_roots(dg, gpm.GPM_APP_CLIQUE, 7, sample, per_root=True)
     assert int(c[0]) == data["k8_sample"]["cliques"]["7"]
     assert [int(x) for x in pr] == [want.get(int(r), (0, 0))[0] for r in sample]
+
+
+# ------------------------------------------------------- 8-vertex motifs
+
+def test_motif_k8():
+    """8-vertex motifs (11,117 patterns; counted leaf by leaf into global
+    pattern counters): the oracle's ESU route per pattern on two random
+    graphs, closed forms on a path and a star, and the star identity
+    sum_p dom(p) count_p = sum_v C(d(v), 7) on a sparse random graph."""
+    for g in (G.gnp(40, 0.1, 2), G.gnp(28, 0.16, 5)):
+        dg = gpm.graph_from_csr(g)
+        assert motif_by_code(dg, 8) == O.motif_count(g, 8, method="esu")
+    dg = gpm.graph_from_csr(G.path(20))
+    assert list(motif_by_code(dg, 8).values()) == [13]
+    dg = gpm.graph_from_csr(G.star(12))
+    assert list(motif_by_code(dg, 8).values()) == [comb(12, 7)]
+    g = G.gnp(400, 0.012, 9)
+    dg = gpm.graph_from_csr(g)
+    c8 = gpm.gpm_motif_count(dg, 8)
+    lhs = sum(_dominating(8, gpm.gpm_motif_pattern(8, p)) * int(c) for p, c in enumerate(c8) if c)
+    assert lhs == sum(comb(int(x), 7) for x in g.degrees())
+    assert int(c8.sum()) > 0
