@@ -176,7 +176,8 @@ typedef struct {
                                /* has at least this many entries left counts its last two levels by  */
                                /* entry class instead of leaf by leaf (0: never)                     */
     int32_t clique_compact3;   /* three-level clique tail on the node's members whenever that        */
-                               /* shortens the rows: 1 (default) or 0                                */
+                               /* shortens the rows: 0 never, 1 (default), 2 also with the pairs of  */
+                               /* nodes of at most 64 members taken one at a time by the whole warp  */
     int32_t batch_split;       /* batched launch: roots heavier than 1/4096 of the total estimated   */
                                /* work are cut into this many units over ranges of their children    */
                                /* before the launch (0 or 1: none; at most 64)                       */
@@ -206,6 +207,36 @@ typedef struct {
 } gpm_stats;
 
 gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
+
+/*
+ * The paper's load balancing, for comparison with the in-kernel hand-off
+ * (Section 4.3.5: the CPU watches the share of active warps, stops the
+ * kernel when it falls below a threshold -- 40 % for cliques and 10 % for
+ * motifs in the paper's experiments -- redistributes the unfinished work and
+ * relaunches).  Here: the kernel runs without donation over every root; the
+ * host polls the number of warps holding work; once every root has been
+ * handed out and fewer than threshold x warps still hold work, it raises a
+ * stop flag, every busy warp writes its remaining work (one unit per level
+ * with children left) to a spill buffer and leaves, and the host relaunches
+ * over the spilled units, until a launch spills nothing.
+ *   app, k    : GPM_APP_CLIQUE (3 <= k <= 16) or GPM_APP_MOTIF (3 <= k <= 8).
+ *   threshold : 0 <= threshold <= 1 (0: never stop, the plain launch without
+ *               donation).
+ *   counts    : as gpm_count_roots over every root.
+ *   stats     : nullable; launches, units spilled, summed kernel time and the
+ *               whole loop's host time.
+ * Same counts as gpm_clique_count / gpm_motif_count.  Errors as those.
+ */
+typedef struct {
+    int32_t launches;
+    int32_t pad;
+    int64_t spilled_units;
+    double kernel_ms;
+    double wall_ms;
+} gpm_monitor_stats;
+
+gpm_status gpm_count_monitored(gpm_graph* g, int app, int k, double threshold, uint64_t* counts, int64_t counts_len,
+                               gpm_monitor_stats* stats);
 
 /* ------------------------------------------------------------------------
  * Learned scheduler (not in the paper; changes only the order and splitting

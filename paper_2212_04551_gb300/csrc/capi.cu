@@ -295,6 +295,38 @@ gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, i
     });
 }
 
+gpm_status gpm_count_monitored(gpm_graph* g, int app, int k, double threshold, uint64_t* counts, int64_t counts_len,
+                               gpm_monitor_stats* stats) {
+    return guarded([&] {
+        check_graph(g);
+        if (!counts) fail(GPM_EINVAL, "counts is NULL");
+        if (!(threshold >= 0.0 && threshold <= 1.0)) fail(GPM_EINVAL, "threshold must be in [0, 1]");
+        MonitorStats ms{};
+        std::vector<uint64_t> c;
+        if (app == GPM_APP_CLIQUE) {
+            if (counts_len < 1) fail(GPM_EINVAL, "counts_len < 1");
+            c.assign(1, 0);
+            run_clique_monitored(g, k, threshold, c.data(), &ms);
+        } else if (app == GPM_APP_MOTIF) {
+            if (k < 3 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "k out of range [3, 8]");
+            const PatternTable& t = pattern_table(k);
+            if (counts_len < t.num_patterns) fail(GPM_EINVAL, "counts_len smaller than the number of patterns");
+            c.assign(t.num_patterns, 0);
+            run_motif_monitored(g, k, threshold, c.data(), &ms);
+        } else {
+            fail(GPM_EINVAL, "unknown app");
+        }
+        std::memcpy(counts, c.data(), sizeof(uint64_t) * c.size());
+        if (stats) {
+            stats->launches = ms.launches;
+            stats->pad = 0;
+            stats->spilled_units = ms.spilled_units;
+            stats->kernel_ms = ms.kernel_ms;
+            stats->wall_ms = ms.wall_ms;
+        }
+    });
+}
+
 gpm_status gpm_get_config(const gpm_graph* g, gpm_config* out) {
     return guarded([&] {
         check_graph(g);
@@ -319,7 +351,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.clique_tail != 0 && c.clique_tail != 2 && c.clique_tail != 3) fail(GPM_EINVAL, "clique_tail must be 0, 2 or 3");
         if (c.clique_compact < 0 || c.clique_compact > 2) fail(GPM_EINVAL, "clique_compact must be 0, 1 or 2");
         if (c.motif_agg_min < 0) fail(GPM_EINVAL, "motif_agg_min < 0");
-        if (c.clique_compact3 != 0 && c.clique_compact3 != 1) fail(GPM_EINVAL, "clique_compact3 must be 0 or 1");
+        if (c.clique_compact3 < 0 || c.clique_compact3 > 2) fail(GPM_EINVAL, "clique_compact3 must be 0, 1 or 2");
         if (c.batch_split < 0 || c.batch_split > 64) fail(GPM_EINVAL, "batch_split must be in [0, 64]");
         g->cfg = c;
     });

@@ -37,6 +37,7 @@
 
 #include "common.cuh"
 #include "clique_dev.cuh"
+#include "monitor.cuh"
 
 namespace gpm {
 
@@ -68,6 +69,9 @@ struct CliqueParams {
     int tail_levels;
     int compact;
     int compact3;
+    int monitor;                // host-monitored balancing (no donation): count active warps, obey stop
+    CliqueUnit* spill;
+    unsigned long long spill_cap;
 };
 
 __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
@@ -113,6 +117,9 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     walk.tail_levels = p.tail_levels;
     walk.compact = p.compact;
     walk.compact3 = p.compact3;
+    walk.monitor = p.monitor != 0;
+    walk.spill = p.spill;
+    walk.spill_cap = p.spill_cap;
 
     int ovf = 0;                      // a carry-checked sum wrapped (lane-private)
     unsigned long long top_sum = 0;   // lane-private k_hi-clique count
@@ -136,6 +143,7 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     while (!aborted) {
         // ---- acquire a unit: pre-split seeds, then roots, then donated work
         int kind = 0;
+        if (lane == 0 && p.monitor && *(volatile int*)&ctl->stop) exhausted = true;   // the host redistributes
         if (lane == 0) {
             // seeds and roots only run out once: after that, look at the mailbox alone
             unsigned long long sd = exhausted ? ~0ull : *(volatile unsigned long long*)&ctl->next_seed;
@@ -210,6 +218,7 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         idle = false;
         spin = 0;
         const unsigned long long t_unit = gpm_globaltimer();
+        if (p.monitor && lane == 0) atomicAdd(&ctl->active, 1);
 
         // ---- process the unit
         const int root_pos = unit->root_pos;
@@ -228,6 +237,7 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         if (lane == 0) {
             atomicAdd(&ctl->units_done, 1ull);
             atomicAdd((unsigned long long*)&ctl->pending, (unsigned long long)-1ll);
+            if (p.monitor) atomicSub(&ctl->active, 1);
         }
         busy += gpm_globaltimer() - t_unit;
     }
@@ -286,6 +296,84 @@ __global__ void k_clique_small(const int32_t* __restrict__ outdeg, const int32_t
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(&ctl->counts[k], local);
 }
 
+// Launch geometry, shared-memory layout and work-queue buffers of one
+// k_clique launch over n_counter counter roots and n_seed seed units (room
+// for extra_units more units beside the seeds: the monitored form's spill
+// buffers).  Fills every field of p except ctl, per_root and the modes.
+struct CliqueLaunch {
+    CliqueParams p{};
+    Grid gr;
+    int wpb = 0;
+    size_t smem = 0;
+    CliqueUnit* seeds = nullptr;
+    CliqueUnit* extra = nullptr;
+};
+
+static CliqueLaunch plan_clique_launch(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_counter,
+                                       unsigned long long n_seed, unsigned long long extra_units) {
+    if (g->max_outdeg > CQ_MAX_OUTDEG)
+        fail(GPM_ENOTIMPL, "oriented out-degree " + std::to_string(g->max_outdeg) + " exceeds the bitmap limit of " +
+                               std::to_string(CQ_MAX_OUTDEG));
+    CliqueLaunch c;
+    CliqueParams& p = c.p;
+    cudaStream_t s = g->stream;
+    p.off = g->dag_off.as<int32_t>();
+    p.adj = g->dag_adj.as<int32_t>();
+    p.outdeg = g->dag_outdeg.as<int32_t>();
+    p.deg = g->degree.as<int32_t>();
+    p.roots = d_roots;
+    p.n_roots = n_counter;
+    p.k_lo = std::max(k_lo, 3);
+    p.k_hi = k_hi;
+    p.maxd = std::max(g->max_outdeg, 1);
+    p.wmax = (p.maxd + 31) / 32;
+    p.compact = g->cfg.clique_compact;   // before the layout: it sizes the compaction region
+    // the compacted three-level tail runs where the three-level tail does
+    const bool three = k_hi >= 5 && (g->cfg.clique_tail == 3 || (g->cfg.clique_tail == 0 && k_hi >= 7));
+    p.compact3 = three ? g->cfg.clique_compact3 : 0;
+    const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0 || p.compact3 != 0);
+    p.stride_words = L.total;
+    int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block
+                                          : best_warps_per_block((const void*)k_clique, (size_t)L.total * 4, 0);
+    size_t smem = (size_t)wpb * L.total * 4;
+    while (smem > 227 * 1024 && wpb > 1) {
+        wpb /= 2;
+        smem = (size_t)wpb * L.total * 4;
+    }
+    if (smem > 227 * 1024) fail(GPM_ENOTIMPL, "clique bitmap does not fit in shared memory");
+    GPM_CUDA(cudaFuncSetAttribute(k_clique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    c.gr = plan_grid(g, (const void*)k_clique, wpb, smem);
+    c.wpb = wpb;
+    c.smem = smem;
+    // idle ring (capacity: a power of two >= every warp), mailboxes, seeds
+    unsigned long long cap = 1;
+    while (cap < (unsigned long long)c.gr.total_warps()) cap <<= 1;
+    const size_t stride = (sizeof(MailHdr) + sizeof(CliqueUnit) + 127) & ~size_t(127);
+    const size_t ring_bytes = (sizeof(QSeq) + sizeof(int32_t)) * cap;
+    const size_t mbox_bytes = stride * (size_t)c.gr.total_warps();
+    const size_t seed_bytes = sizeof(CliqueUnit) * std::max<unsigned long long>(n_seed, 1);
+    const size_t extra_bytes = sizeof(CliqueUnit) * extra_units;
+    g->scratch_queue.ensure(ring_bytes + mbox_bytes + seed_bytes + extra_bytes + 256);
+    unsigned char* qb = g->scratch_queue.as<unsigned char>();
+    p.ring_seq = reinterpret_cast<QSeq*>(qb);
+    p.ring_ids = reinterpret_cast<int32_t*>(qb + sizeof(QSeq) * cap);
+    p.ring_cap = cap;
+    p.mbox = qb + ((ring_bytes + 127) & ~size_t(127));
+    p.mbox_stride = (int)stride;
+    c.seeds = reinterpret_cast<CliqueUnit*>(p.mbox + mbox_bytes);
+    c.extra = extra_units ? c.seeds + std::max<unsigned long long>(n_seed, 1) : nullptr;
+    p.seeds = c.seeds;
+    p.n_seeds = (long long)n_seed;
+    k_queue_init<<<16, 256, 0, s>>>(p.ring_seq, cap);
+    GPM_CUDA(cudaMemsetAsync(p.mbox, 0, mbox_bytes, s));
+    p.donate = g->cfg.donate;
+    p.donate_min = std::max(2, g->cfg.donate_min);
+    p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
+    p.tail_levels = g->cfg.clique_tail;
+    p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
+    return c;
+}
+
 void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
                 unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, const SplitPlan* plan) {
     if (k_lo < 1 || k_hi > GPM_CLIQUE_MAX_K || k_lo > k_hi) fail(GPM_EINVAL, "bad clique size range");
@@ -322,71 +410,19 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
             GPM_CUDA(cudaGetLastError());
         }
     } else if (n_roots > 0) {
-        if (g->max_outdeg > CQ_MAX_OUTDEG)
-            fail(GPM_ENOTIMPL, "oriented out-degree " + std::to_string(g->max_outdeg) +
-                                   " exceeds the bitmap limit of " + std::to_string(CQ_MAX_OUTDEG));
-        CliqueParams p{};
-        p.off = g->dag_off.as<int32_t>();
-        p.adj = g->dag_adj.as<int32_t>();
-        p.outdeg = g->dag_outdeg.as<int32_t>();
-        p.deg = g->degree.as<int32_t>();
-        p.roots = d_roots;
-        p.n_roots = n_counter;
-        p.k_lo = std::max(k_lo, 3);
-        p.k_hi = k_hi;
-        p.maxd = std::max(g->max_outdeg, 1);
-        p.wmax = (p.maxd + 31) / 32;
-        p.compact = g->cfg.clique_compact;   // before the layout: it sizes the compaction region
-        // the compacted three-level tail runs where the three-level tail does
-        const bool three = k_hi >= 5 && (g->cfg.clique_tail == 3 || (g->cfg.clique_tail == 0 && k_hi >= 7));
-        p.compact3 = (three && g->cfg.clique_compact3) ? 1 : 0;
-        const CqLayout L = cq_layout(p.maxd, p.wmax, p.compact != 0 || p.compact3 != 0);
-        p.stride_words = L.total;
-        int wpb = g->cfg.warps_per_block > 0 ? g->cfg.warps_per_block
-                                              : best_warps_per_block((const void*)k_clique, (size_t)L.total * 4, 0);
-        size_t smem = (size_t)wpb * L.total * 4;
-        while (smem > 227 * 1024 && wpb > 1) {
-            wpb /= 2;
-            smem = (size_t)wpb * L.total * 4;
-        }
-        if (smem > 227 * 1024) fail(GPM_ENOTIMPL, "clique bitmap does not fit in shared memory");
-        GPM_CUDA(cudaFuncSetAttribute(k_clique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        Grid gr = plan_grid(g, (const void*)k_clique, wpb, smem);
-        // idle ring (capacity: a power of two >= every warp), mailboxes, seeds
-        unsigned long long cap = 1;
-        while (cap < (unsigned long long)gr.total_warps()) cap <<= 1;
-        const size_t stride = (sizeof(MailHdr) + sizeof(CliqueUnit) + 127) & ~size_t(127);
-        const size_t ring_bytes = (sizeof(QSeq) + sizeof(int32_t)) * cap;
-        const size_t mbox_bytes = stride * (size_t)gr.total_warps();
-        const size_t seed_bytes = sizeof(CliqueUnit) * std::max<unsigned long long>(n_seed, 1);
-        g->scratch_queue.ensure(ring_bytes + mbox_bytes + seed_bytes + 256);
-        unsigned char* qb = g->scratch_queue.as<unsigned char>();
-        p.ring_seq = reinterpret_cast<QSeq*>(qb);
-        p.ring_ids = reinterpret_cast<int32_t*>(qb + sizeof(QSeq) * cap);
-        p.ring_cap = cap;
-        p.mbox = qb + ((ring_bytes + 127) & ~size_t(127));
-        p.mbox_stride = (int)stride;
-        CliqueUnit* seeds = reinterpret_cast<CliqueUnit*>(p.mbox + mbox_bytes);
-        p.seeds = seeds;
-        p.n_seeds = (long long)n_seed;
-        k_queue_init<<<16, 256, 0, s>>>(p.ring_seq, cap);
-        GPM_CUDA(cudaMemsetAsync(p.mbox, 0, mbox_bytes, s));
+        CliqueLaunch L = plan_clique_launch(g, k_lo, k_hi, d_roots, n_counter, n_seed, 0);
+        CliqueParams& p = L.p;
         if (n_split > 0)
             k_clique_seed<<<(n_split + 127) / 128, 128, 0, s>>>(d_roots, n_counter, n_split, split_chunks,
-                                                               chunk_off, k_hi, p.outdeg, seeds);
+                                                               chunk_off, k_hi, p.outdeg, L.seeds);
         p.ctl = ctl;
         p.per_root = d_per_root;
-        p.donate = g->cfg.donate;
-        p.donate_min = std::max(2, g->cfg.donate_min);
-        p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
-        p.tail_levels = g->cfg.clique_tail;
-        p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
         GPM_CUDA(cudaEventRecord(g->ev0, s));
-        k_clique<<<gr.blocks, wpb * 32, smem, s>>>(p);
+        k_clique<<<L.gr.blocks, L.wpb * 32, L.smem, s>>>(p);
         GPM_CUDA(cudaGetLastError());
         GPM_CUDA(cudaEventRecord(g->ev1, s));
-        st.grid_blocks = gr.blocks;
-        st.warps_per_block = wpb;
+        st.grid_blocks = L.gr.blocks;
+        st.warps_per_block = L.wpb;
     }
     GPM_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
     GPM_CUDA(cudaStreamSynchronize(s));
@@ -406,6 +442,59 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
     if (h.overflow) fail(GPM_EOVERFLOW, "clique count exceeds 2^64-1");
     for (int j = k_lo; j <= k_hi; j++) counts_out[j - k_lo] = h.counts[j];
+}
+
+// The paper's load balancing (Section 4.3.5), for comparison with the
+// in-kernel hand-off: see monitor.cuh.  Counts add up over the launches.
+void run_clique_monitored(gpm_graph* g, int k, double threshold, uint64_t* count_out, MonitorStats* ms_out) {
+    if (k < 3 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "monitored clique counting needs 3 <= k <= 16");
+    ensure_dag(g);
+    cudaStream_t s = g->stream;
+    const int32_t* d_roots = ensure_root_order(g, GPM_APP_CLIQUE);
+    const int64_t n_roots = g->n;
+    g->scratch_small.ensure(sizeof(Control));
+    Control* ctl = g->scratch_small.as<Control>();
+    MonitorStats ms{};
+    unsigned __int128 total = 0;
+    gpm_stats st{};
+    if (n_roots > 0) {
+        // spill capacity: one unit per level per warp; two buffers used in
+        // turn (the last launch's spill is the next launch's seeds)
+        const Grid probe = plan_clique_launch(g, k, k, d_roots, n_roots, 0, 0).gr;
+        const unsigned long long cap = (unsigned long long)probe.total_warps() * CQ_LEVELS;
+        CliqueLaunch L = plan_clique_launch(g, k, k, d_roots, n_roots, cap, cap);
+        CliqueUnit* bufs[2] = {L.seeds, L.extra};
+        auto launch = [&](long long counter_roots, unsigned long long n_seeds, int turn) {
+            CliqueParams p = L.p;
+            p.ctl = ctl;
+            p.per_root = nullptr;
+            p.donate = 0;
+            p.monitor = 1;
+            p.n_roots = counter_roots;
+            p.seeds = bufs[turn];
+            p.n_seeds = (long long)n_seeds;
+            p.spill = bufs[turn ^ 1];
+            p.spill_cap = cap;
+            GPM_CUDA(cudaEventRecord(g->ev0, s));
+            k_clique<<<L.gr.blocks, L.wpb * 32, L.smem, s>>>(p);
+            GPM_CUDA(cudaGetLastError());
+            GPM_CUDA(cudaEventRecord(g->ev1, s));
+        };
+        auto after = [&](const Control& h) {
+            total += h.counts[k];
+            st.word_ops += h.word_ops;
+            st.units_done += h.units_done;
+        };
+        ms = monitored_loop(g, ctl, L.gr.total_warps(), n_roots, threshold, cap, launch, after);
+        st.grid_blocks = L.gr.blocks;
+        st.warps_per_block = L.wpb;
+        st.kernel_ms = ms.kernel_ms;
+        st.kernel_launches = ms.launches;
+    }
+    g->stats = st;
+    if (total >> 64) fail(GPM_EOVERFLOW, "clique count exceeds 2^64-1");
+    *count_out = (uint64_t)total;
+    if (ms_out) *ms_out = ms;
 }
 
 }  // namespace gpm

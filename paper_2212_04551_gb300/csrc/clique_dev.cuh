@@ -222,7 +222,14 @@ struct CliqueWalk {
     unsigned long long donate_after_ns;   // a unit splits only after running this long
     int tail_levels;                      // 2 or 3 (0: 3)
     int compact;                          // compacted two-level tail: 0 never, 1 large nodes, 2 whenever shorter
-    int compact3;                         // compacted three-level tail whenever it shortens the rows
+    int compact3;                         // compacted three-level tail whenever it shortens the rows (2: and
+                                          // warp-cooperative pairs for nodes of at most 64 members)
+    // host-monitored balancing (the paper's stop / redistribute / restart):
+    // when the host raises ctl->stop, the walk writes its remaining work as
+    // units to spill[] and unwinds
+    bool monitor;
+    CliqueUnit* spill;
+    unsigned long long spill_cap;
     __device__ uint32_t* pairs_u32() const { return reinterpret_cast<uint32_t*>(pairs); }
 };
 
@@ -540,7 +547,7 @@ template <int W2>
 __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows, int w, int c, int from, int to,
                                           int* mem, uint32_t* R, unsigned long long& n3, unsigned long long& n2,
                                           unsigned long long& km1, unsigned long long& kk,
-                                          unsigned long long& wops, int lane) {
+                                          unsigned long long& wops, int lane, bool coop) {
     int n = 0, m_lo = 0, m_hi = 0;
     for (int q = 0; q < w; q++) {
         const uint32_t word = C[q];
@@ -577,6 +584,43 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
     __syncwarp();
     if (lane == 0) wops += (unsigned long long)c * (unsigned)w2;
     n3 += (unsigned)(m_hi - m_lo);
+    if (W2 <= 2 && coop) {
+        // at most 64 members: the warp takes the pairs one at a time, lane t
+        // holding the rows of members t and t + 32, and for a pair with
+        // candidates y adds popc(y & R[t]) when t is in y -- every lane works
+        // on every pair, whatever |y|, instead of one lane looping over it
+        const uint32_t ra0 = lane < c ? R[lane * ws2] : 0u;
+        const uint32_t ra1 = (W2 == 2 && lane < c) ? R[lane * ws2 + (W2 == 2 ? 1 : 0)] : 0u;
+        const uint32_t rb1 = (W2 == 2 && lane + 32 < c) ? R[(lane + 32) * ws2 + (W2 == 2 ? 1 : 0)] : 0u;
+        unsigned long long npairs = 0, mine = 0, g_all = 0;
+        for (int m1 = m_lo; m1 < m_hi; m1++) {
+            const uint32_t x0 = R[m1 * ws2];
+            const uint32_t x1 = W2 == 2 ? R[m1 * ws2 + (W2 == 2 ? 1 : 0)] : 0u;
+#pragma unroll
+            for (int q2 = 0; q2 < W2; q2++) {
+                uint32_t bits = q2 == 0 ? x0 : x1;
+                while (bits) {
+                    const int m2 = 32 * q2 + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const uint32_t y0 = x0 & R[m2 * ws2];
+                    const uint32_t y1 = W2 == 2 ? (x1 & R[m2 * ws2 + (W2 == 2 ? 1 : 0)]) : 0u;
+                    npairs++;
+                    g_all += (unsigned)(__popc(y0) + __popc(y1));
+                    unsigned v = ((y0 >> lane) & 1u) ? (unsigned)(__popc(y0 & ra0) + __popc(y1 & ra1)) : 0u;
+                    if (W2 == 2) v += ((y1 >> lane) & 1u) ? (unsigned)__popc(y1 & rb1) : 0u;
+                    mine += v;
+                }
+            }
+        }
+        kk += mine;
+        n2 += npairs;
+        if (lane == 0) {
+            km1 += g_all;
+            wops += (g_all + npairs) * (unsigned)w2;
+        }
+        __syncwarp();
+        return;
+    }
     int np = 0;
     for (int m1 = m_lo; m1 < m_hi; m1++) {
         const uint32_t* r1 = R + m1 * ws2;
@@ -606,13 +650,14 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
 __device__ __forceinline__ void cq_tail3c_dispatch(const uint32_t* C, const TriRows& rows, int w, int c, int from,
                                                    int to, int* mem, uint32_t* R, unsigned long long& n3,
                                                    unsigned long long& n2, unsigned long long& km1,
-                                                   unsigned long long& kk, unsigned long long& wops, int lane) {
+                                                   unsigned long long& kk, unsigned long long& wops, int lane,
+                                                   bool coop) {
     const int w2 = (c + 31) >> 5;
-    if (w2 <= 1) cq_tail3c<1>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
-    else if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
-    else if (w2 <= 3) cq_tail3c<3>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
-    else if (w2 <= 4) cq_tail3c<4>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
-    else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane);
+    if (w2 <= 1) cq_tail3c<1>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop);
+    else if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop);
+    else if (w2 <= 3) cq_tail3c<3>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false);
+    else if (w2 <= 4) cq_tail3c<4>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false);
+    else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false);
 }
 
 // Split point of a node's remaining children (set bits of C in [from, to))
@@ -721,7 +766,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
             const int w2 = (c + 31) >> 5;
             if (c > 0 && w2 <= CQ_CW && w2 < w)
                 cq_tail3c_dispatch(Cs, rows, w, c, cur[s], hiv[s], list, a.pairs_u32(), n3, n2, km1, unit_sum, wops,
-                                   lane);
+                                   lane, a.compact3 == 2);
             else
                 cq_tail3_dispatch(Cs, rows, w, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
             if (lane == 0) {
@@ -804,7 +849,7 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
         // at most once per CQ_CHECK_NS
         int chk = 0;
         unsigned long long now = 0;
-        if (DONATE && (big || (++iter & 15) == 0)) {
+        if ((DONATE || a.monitor) && (big || (++iter & 15) == 0)) {
             big = false;
             if (lane == 0) {
                 now = gpm_globaltimer();
@@ -814,6 +859,41 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
                 }
             }
             chk = __shfl_sync(GPM_FULL_MASK, chk, 0);
+        }
+        if (!DONATE && a.monitor && chk) {
+            Control* ctl = a.ctl;
+            int err = 0, stop = 0;
+            if (lane == 0) {
+                err = *(volatile int*)&ctl->error;
+                stop = *(volatile int*)&ctl->stop;
+            }
+            err = __shfl_sync(GPM_FULL_MASK, err, 0);
+            if (err) return false;
+            if (__shfl_sync(GPM_FULL_MASK, stop, 0)) {
+                // spill every level's remaining children as a unit, then
+                // unwind (the emptied ranges end the walk)
+                if (lane == 0) {
+                    for (int t = s_base; t <= s; t++) {
+                        if (cur[t] >= hiv[t]) continue;
+                        const unsigned long long slot = atomicAdd(&ctl->spill_n, 1ull);
+                        if (slot >= a.spill_cap) {   // never: one unit per level per warp fits
+                            atomicCAS(&ctl->error, 0, DEV_ECHECK + 7);
+                            break;
+                        }
+                        CliqueUnit u;
+                        u.root_pos = root_pos;
+                        u.depth = depth + (t - s_base);
+                        u.lo = cur[t];
+                        u.hi = hiv[t];
+                        for (int z = 0; z < depth; z++) u.path[z] = unit->path[z];
+                        for (int z = s_base; z < t; z++) u.path[depth + (z - s_base)] = (uint16_t)(cur[z] - 1);
+                        for (int z = u.depth; z < GPM_CLIQUE_MAX_K; z++) u.path[z] = 0;
+                        a.spill[slot] = u;
+                    }
+                    for (int t = s_base; t <= s; t++) hiv[t] = cur[t];
+                }
+                __syncwarp();
+            }
         }
         if (DONATE && chk) {
             Control* ctl = a.ctl;

@@ -136,7 +136,10 @@ struct alignas(128) Control {
     unsigned long long next_seed;     // next pre-split seed unit
     alignas(128) long long pending;   // roots + donated units not yet finished
     int error;                        // GPM_* status raised on the device
-    int idle;                         // (unused)
+    int stop;                         // host-monitored balancing: spill the remaining work and leave
+    alignas(128) int active;          // host-monitored balancing: warps holding a unit
+    int pad_active;
+    unsigned long long spill_n;       // host-monitored balancing: units spilled so far
     alignas(128) unsigned long long q_head;   // (alignas binds per declarator: one per line)
     unsigned long long q_tail;
     alignas(128) unsigned long long donations;
@@ -188,6 +191,16 @@ struct SplitPlan {
     int64_t n_seeds = 0;
 };
 
+// Host-monitored balancing (the paper's stop / redistribute / restart)
+struct MonitorStats {
+    int32_t launches = 0;
+    int64_t spilled_units = 0;
+    double kernel_ms = 0.0;   // sum over the launches
+    double wall_ms = 0.0;     // the whole loop, host monitor included
+};
+void run_clique_monitored(gpm_graph* g, int k, double threshold, uint64_t* count_out, MonitorStats* ms);
+void run_motif_monitored(gpm_graph* g, int k, double threshold, uint64_t* counts_out, MonitorStats* ms);
+
 // clique.cu / motif.cu
 // d_roots[0 .. n_roots): the roots; the first n_counter are handed out one by
 // one, the rest are pre-split as `plan` says (n_counter < 0: no pre-split).
@@ -197,7 +210,8 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
                 const SplitPlan* plan = nullptr);
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
-               const SplitPlan* plan = nullptr);
+               const SplitPlan* plan = nullptr, double monitor_threshold = -1.0,
+               MonitorStats* monitor_stats = nullptr);
 
 // sched.cu
 void root_features(gpm_graph* g, int k, float* d_out);

@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "monitor.cuh"
 #include "motif_dev.cuh"
 
 namespace gpm {
@@ -52,6 +53,9 @@ struct MotifParams {
     unsigned long long* counts; // npat global counters
     int agg_min;                // aggregated last two levels from this many entries (0: never)
     int agg_words;              // shared words of class counters per warp (mt_agg_words(k))
+    int monitor;                // host-monitored balancing (no donation): count active warps, obey stop
+    MotifUnit* spill;
+    unsigned long long spill_cap;
 };
 
 // GCOUNT: count patterns straight into the global counters (k = 8) instead
@@ -89,6 +93,9 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     a.err = &ctl->error;
     a.agg = p.agg_words > 0 ? agg : nullptr;
     a.agg_min = p.agg_words > 0 ? p.agg_min : 0;
+    a.monitor = p.monitor != 0;
+    a.spill = p.spill;
+    a.spill_cap = p.spill_cap;
     if (SMEM_STATE) {
         unsigned char* tail = smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb +
                               sizeof(uint32_t) * (size_t)p.agg_words * nwb;
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     while (!aborted) {
         // ---- acquire a unit: pre-split seeds, then roots, then donated work
         int kind = 0;
+        if (lane == 0 && p.monitor && atomicAdd(&ctl->stop, 0)) exhausted = true;   // the host redistributes
         if (lane == 0) {
             // seeds and roots only run out once: after that, look at the mailbox alone
             unsigned long long sd = exhausted ? ~0ull : *(volatile unsigned long long*)&ctl->next_seed;
@@ -197,6 +205,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         idle = false;
         const unsigned long long t_unit = gpm_globaltimer();
         spin = 0;
+        if (p.monitor && lane == 0) atomicAdd(&ctl->active, 1);
 
         // ---------------------------------------------------- set up the unit
         // (a root, a pre-split range of a root's children, or a donated
@@ -231,6 +240,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         if (lane == 0) {
             atomicAdd(&ctl->units_done, 1ull);
             atomicAdd((unsigned long long*)&ctl->pending, (unsigned long long)-1ll);
+            if (p.monitor) atomicSub(&ctl->active, 1);
         }
         busy += gpm_globaltimer() - t_unit;
     }
@@ -279,7 +289,9 @@ __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_coun
 }
 
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
-               unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, const SplitPlan* plan) {
+               unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, const SplitPlan* plan,
+               double monitor_threshold, MonitorStats* monitor_stats) {
+    const bool monitored = monitor_threshold >= 0.0;
     if (k < 1 || k > MT_MAXK) fail(GPM_ENOTIMPL, "motif size k=" + std::to_string(k) + " not built");
     const PatternTable& tab = pattern_table(k);
     const int npat = (int)tab.num_patterns;
@@ -422,14 +434,16 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
         GPM_CUDA(cudaMemsetAsync(d_per_root, 0, sizeof(unsigned long long) * n_roots, s));
 
     // idle ring (capacity: a power of two >= every warp), mailboxes, seeds
-    p.donate = g->cfg.donate;
+    // (monitored: two spill buffers of one unit per level per warp instead)
+    p.donate = monitored ? 0 : g->cfg.donate;
     unsigned long long cap = 1;
     while (cap < (unsigned long long)nw) cap <<= 1;
+    const unsigned long long spill_cap = monitored ? (unsigned long long)nw * (MT_MAXK + 1) : 0ull;
     const size_t stride = (sizeof(MailHdr) + sizeof(MotifUnit) + 127) & ~size_t(127);
     const size_t ring_bytes = (sizeof(QSeq) + sizeof(int32_t)) * cap;
     const size_t mbox_bytes = p.donate ? stride * (size_t)nw : 0;
-    const size_t seed_bytes = sizeof(MotifUnit) * std::max<unsigned long long>(n_seed, 1);
-    g->scratch_queue.ensure(ring_bytes + mbox_bytes + seed_bytes + 256);
+    const size_t seed_bytes = sizeof(MotifUnit) * std::max<unsigned long long>(std::max(n_seed, spill_cap), 1);
+    g->scratch_queue.ensure(ring_bytes + mbox_bytes + seed_bytes * (monitored ? 2 : 1) + 256);
     unsigned char* qb = g->scratch_queue.as<unsigned char>();
     p.ring_seq = reinterpret_cast<QSeq*>(qb);
     p.ring_ids = reinterpret_cast<int32_t*>(qb + sizeof(QSeq) * cap);
@@ -450,17 +464,53 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
     p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
 
-    if (n_roots > 0) {
+    auto launch_kernel = [&](const MotifParams& q) {
         GPM_CUDA(cudaEventRecord(g->ev0, s));
         if (smem_state) {
-            if (gcount) k_motif<true, true><<<gr.blocks, wpb * 32, smem, s>>>(p);
-            else k_motif<true, false><<<gr.blocks, wpb * 32, smem, s>>>(p);
+            if (gcount) k_motif<true, true><<<gr.blocks, wpb * 32, smem, s>>>(q);
+            else k_motif<true, false><<<gr.blocks, wpb * 32, smem, s>>>(q);
         } else {
-            if (gcount) k_motif<false, true><<<gr.blocks, wpb * 32, smem, s>>>(p);
-            else k_motif<false, false><<<gr.blocks, wpb * 32, smem, s>>>(p);
+            if (gcount) k_motif<false, true><<<gr.blocks, wpb * 32, smem, s>>>(q);
+            else k_motif<false, false><<<gr.blocks, wpb * 32, smem, s>>>(q);
         }
         GPM_CUDA(cudaGetLastError());
         GPM_CUDA(cudaEventRecord(g->ev1, s));
+    };
+    if (monitored && n_roots > 0) {
+        // stop / redistribute / restart (monitor.cuh); the pattern counters
+        // add up over the launches
+        MotifUnit* bufs[2] = {seeds, seeds + std::max<unsigned long long>(std::max(n_seed, spill_cap), 1)};
+        auto launch = [&](long long counter_roots, unsigned long long n_seeds, int turn) {
+            MotifParams q = p;
+            q.monitor = 1;
+            q.n_roots = counter_roots;
+            q.seeds = bufs[turn];
+            q.n_seeds = (long long)n_seeds;
+            q.spill = bufs[turn ^ 1];
+            q.spill_cap = spill_cap;
+            launch_kernel(q);
+        };
+        unsigned long long wops = 0, units = 0;
+        auto after = [&](const Control& hc) {
+            wops += hc.word_ops;
+            units += hc.units_done;
+        };
+        const MonitorStats ms = monitored_loop(g, ctl, (int)nw, n_counter, monitor_threshold, spill_cap, launch, after);
+        if (monitor_stats) *monitor_stats = ms;
+        GPM_CUDA(cudaMemcpyAsync(host.data(), p.counts, sizeof(unsigned long long) * npat, cudaMemcpyDeviceToHost, s));
+        GPM_CUDA(cudaStreamSynchronize(s));
+        st.grid_blocks = gr.blocks;
+        st.warps_per_block = wpb;
+        st.kernel_ms = ms.kernel_ms;
+        st.kernel_launches = ms.launches;
+        st.word_ops = wops;
+        st.units_done = units;
+        g->stats = st;
+        for (int j = 0; j < npat; j++) counts_out[j] = host[j];
+        return;
+    }
+    if (n_roots > 0) {
+        launch_kernel(p);
         st.grid_blocks = gr.blocks;
         st.warps_per_block = wpb;
     }
@@ -486,6 +536,11 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
     if (h.overflow) fail(GPM_EOVERFLOW, "a pattern count exceeds 2^64-1");
     for (int j = 0; j < npat; j++) counts_out[j] = host[j];
+}
+
+void run_motif_monitored(gpm_graph* g, int k, double threshold, uint64_t* counts_out, MonitorStats* ms) {
+    if (k < 3 || k > MT_MAXK) fail(GPM_EINVAL, "monitored motif counting needs 3 <= k <= 8");
+    run_motif(g, k, nullptr, 0, nullptr, counts_out, -1, nullptr, threshold, ms);
 }
 
 }  // namespace gpm

@@ -89,6 +89,12 @@ struct MotifWalk {
     // agg_min <= 0: never)
     uint32_t* agg;
     int agg_min;
+    // host-monitored balancing (the paper's stop / redistribute / restart):
+    // when the host raises ctl->stop, the walk writes its remaining work as
+    // units to spill[] and unwinds
+    bool monitor;
+    MotifUnit* spill;
+    unsigned long long spill_cap;
 };
 
 // 32-bit words of one warp's class counters for size k: HA, HB, E (one per
@@ -599,6 +605,44 @@ __device__ __forceinline__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdept
             l++;
         }
 
+        if (!DONATE && a.monitor) {
+            Control* ctl = a.ctl;
+            int err = 0, stop = 0;
+            const unsigned long long now = gpm_globaltimer();
+            if (lane == 0 && now - last_check >= MT_CHECK_NS) {
+                last_check = now;
+                err = *(volatile int*)&ctl->error;
+                stop = atomicAdd(&ctl->stop, 0);
+            }
+            err = __shfl_sync(GPM_FULL_MASK, err, 0);
+            if (err) return false;
+            if (__shfl_sync(GPM_FULL_MASK, stop, 0)) {
+                // spill every level's remaining children as a unit (the path,
+                // as a hand-off carries it), then unwind through the emptied
+                // ranges, popping the marks on the way
+                if (lane == 0) {
+                    for (int t = pdepth; t <= l; t++) {
+                        if (W->cur[t] >= W->hi[t]) continue;
+                        const unsigned long long slot = atomicAdd(&ctl->spill_n, 1ull);
+                        if (slot >= a.spill_cap) {   // never: one unit per level per warp fits
+                            atomicCAS(&ctl->error, 0, DEV_ECHECK + 7);
+                            break;
+                        }
+                        MotifUnit* u = a.spill + slot;
+                        u->root_pos = root_pos;
+                        u->depth = t;
+                        u->lo = W->cur[t];
+                        u->hi = W->hi[t];
+                        for (int z = 0; z < MT_MAXK; z++) {
+                            u->sub[z] = z < t ? W->sub[z] : -1;
+                            u->pos[z] = (z >= 1 && z < t) ? W->cur[z] - 1 : -1;
+                        }
+                    }
+                    for (int t = pdepth; t <= l; t++) W->hi[t] = W->cur[t];
+                }
+                __syncwarp();
+            }
+        }
         // donation check: after every step, but at most once per
         // MT_CHECK_NS (the lines it reads are shared by every warp)
         if (DONATE) {

@@ -49,6 +49,11 @@ class gpm_config(ctypes.Structure):
                 ("clique_compact3", ctypes.c_int32), ("batch_split", ctypes.c_int32)]
 
 
+class gpm_monitor_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32), ("pad", ctypes.c_int32), ("spilled_units", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+
 class gpm_stats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("units_done", ctypes.c_uint64),
                 ("donations", ctypes.c_uint64), ("idle_polls", ctypes.c_uint64),
@@ -97,6 +102,8 @@ SIGNATURES = {
     "gpm_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
     "gpm_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
     "gpm_motif_count_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, _u64p, ctypes.c_int64, _vp]),
+    "gpm_count_monitored": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _u64p, ctypes.c_int64,
+                                           ctypes.POINTER(gpm_monitor_stats)]),
     "gpm_selftest_sum": (ctypes.c_int, [_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _u64p]),
     "gpm_measure_l2": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
 }
@@ -253,6 +260,17 @@ def gpm_count_roots(g: Graph, app: int, k: int, roots=None, per_root: bool = Fal
                                 pr.ctypes.data_as(_u64p) if pr is not None else None)
     _check(st, "gpm_count_roots")
     return counts, (pr[:nrep] if pr is not None else None)
+
+
+def gpm_count_monitored(g: Graph, app: int, k: int, threshold: float):
+    """Counts under the paper's host-monitored stop / redistribute / restart
+    balancing: (counts, stats dict)."""
+    ncounts = 1 if app == GPM_APP_CLIQUE else gpm_motif_num_patterns(k)
+    counts = np.zeros(ncounts, dtype=np.uint64)
+    st = gpm_monitor_stats()
+    _check(load().gpm_count_monitored(g, int(app), int(k), float(threshold), counts.ctypes.data_as(_u64p), ncounts,
+                                      ctypes.byref(st)), "gpm_count_monitored")
+    return counts, {f: getattr(st, f) for f, _ in gpm_monitor_stats._fields_ if f != "pad"}
 
 
 def gpm_get_config(g: Graph) -> gpm_config:

@@ -177,6 +177,29 @@ def test_compacted_tail_dense_graphs(compact):
         assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 6)] == want, g.n
 
 
+@pytest.mark.parametrize("compact3", [0, 1, 2])
+def test_three_level_tail_modes(compact3):
+    """The three-level clique tail (k >= 7) on the full-width rows (0), on
+    the node's own members (1), and with the pairs of nodes of at most 64
+    members taken by the whole warp (2): closed forms on K_n and Turan
+    graphs (member sets of 1 to 5 words) and the oracle on dense random
+    graphs and planted blocks."""
+    for n in (40, 70, 97, 150):
+        dg = gpm.graph_from_csr(G.complete(n))
+        gpm.gpm_set_config(dg, clique_compact3=compact3)
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 9)] == [comb(n, k) for k in range(4, 10)], n
+    dg = gpm.graph_from_csr(G.turan(200, 10))
+    gpm.gpm_set_config(dg, clique_compact3=compact3)
+    assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 9)] == [_turan_cliques([20] * 10, k)
+                                                                     for k in range(7, 10)]
+    for g in (G.gnp(120, 0.55, 71), G.sbm(500, 50, 0.6, 0.02, 72)):
+        dg = gpm.graph_from_csr(g)
+        gpm.gpm_set_config(dg, clique_compact3=compact3, donate_after_us=0, donate_min=2)
+        want = [O.clique_count(g, k) for k in (7, 8)]
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 8)] == want, g.n
+        assert [gpm.gpm_clique_count(dg, k) for k in (7, 8)] == want, g.n
+
+
 def test_star_with_large_hub():
     """A hub of degree 300 (motifs) -- a long exclusive list in one step."""
     g = G.star(300)
@@ -242,6 +265,29 @@ def test_schedule_never_changes_counts(cfg):
     gpm.gpm_set_config(dg, **cfg)
     assert [gpm.gpm_clique_count(dg, k) for k in (4, 6)] == ref_c
     assert motif_by_code(dg, 4) == ref_m
+
+
+@pytest.mark.parametrize("threshold", [0.0, 0.4, 0.9])
+def test_monitored_balancing_same_counts(threshold):
+    """The paper's host-monitored stop / redistribute / restart balancing
+    gives the in-kernel hand-off's counts, for cliques and motifs (and 5-
+    and 7-cliques with the deeper tails); at a high threshold the first
+    launch is stopped early and the spilled work relaunched."""
+    g, ref_c, ref_m = _schedule_reference()
+    dg = gpm.graph_from_csr(g)
+    c6, st = gpm.gpm_count_monitored(dg, gpm.GPM_APP_CLIQUE, 6, threshold)
+    assert int(c6[0]) == ref_c[1]
+    m4, st_m = gpm.gpm_count_monitored(dg, gpm.GPM_APP_MOTIF, 4, threshold)
+    assert {gpm.gpm_motif_pattern(4, p): int(x) for p, x in enumerate(m4) if x} == ref_m
+    for k in (5, 7):
+        c, _ = gpm.gpm_count_monitored(dg, gpm.GPM_APP_CLIQUE, k, threshold)
+        assert int(c[0]) == gpm.gpm_clique_count(dg, k), k
+    m5, _ = gpm.gpm_count_monitored(dg, gpm.GPM_APP_MOTIF, 5, threshold)
+    assert np.array_equal(m5, gpm.gpm_motif_count(dg, 5))
+    if threshold == 0.0:
+        assert st["launches"] == 1 and st["spilled_units"] == 0
+    if threshold == 0.9:
+        assert st["launches"] >= 2 and st["spilled_units"] > 0, st
 
 
 # --------------------------------------------------------- invalid inputs
