@@ -534,6 +534,45 @@ def config_sbm2000(stream, learned: Learned) -> dict:
     return res
 
 
+def balancing_ablation(stream) -> dict:
+    """Load balancing on the same kernels and GB300 (the paper's Section
+    4.3.5 and Table optimizations-performance, on this hardware): the
+    in-kernel hand-off (the plain method's default), the paper's
+    host-monitored stop / redistribute / restart (thresholds 40 % for
+    cliques and 10 % for motifs, the paper's best), and no balancing at
+    all.  Workloads: chunglu1m 7-cliques (the headline's deepest size) and
+    sbm2000 6-motifs."""
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    out = {}
+    for name, app, k, th in (("chunglu1m", gpm.GPM_APP_CLIQUE, 7, 0.4), ("sbm2000", gpm.GPM_APP_MOTIF, 6, 0.1)):
+        g = G.workload(name)
+        dg = gpm.graph_from_csr(g, stream=stream)
+        res = {}
+        if app == gpm.GPM_APP_CLIQUE:
+            ref, ms = timed(lambda: gpm.gpm_clique_count(dg, k), stream)
+            ref = np.array([ref], dtype=np.uint64)
+        else:
+            ref, ms = timed(lambda: gpm.gpm_motif_count(dg, k), stream)
+        st = gpm.gpm_get_stats(dg)
+        res["in_kernel_handoff"] = {"ms": ms, "kernel_ms": st["kernel_ms"], "idle_warp_frac": st["idle_warp_frac"],
+                                    "handoffs": int(st["donations"])}
+        t0 = time.perf_counter()
+        c, mst = gpm.gpm_count_monitored(dg, app, k, th)
+        res["host_monitored"] = {"ms": (time.perf_counter() - t0) * 1000.0, "threshold": th, **mst,
+                                 "same_counts": bool(np.array_equal(c, ref))}
+        gpm.gpm_set_config(dg, donate=0)
+        c = gpm.gpm_clique_count(dg, k) if app == gpm.GPM_APP_CLIQUE else gpm.gpm_motif_count(dg, k)
+        st = gpm.gpm_get_stats(dg)
+        res["none"] = {"kernel_ms": st["kernel_ms"], "idle_warp_frac": st["idle_warp_frac"],
+                       "same_counts": bool(np.array_equal(np.ravel(c), np.ravel(ref)))}
+        res["speedup_handoff_vs_monitored"] = res["host_monitored"]["ms"] / res["in_kernel_handoff"]["ms"]
+        res["speedup_handoff_vs_none"] = res["none"]["kernel_ms"] / res["in_kernel_handoff"]["kernel_ms"]
+        out[f"{name}_{'clique' if app == gpm.GPM_APP_CLIQUE else 'motif'}{k}"] = res
+        dg.close()
+    return out
+
+
 def k4_8_entry(dg, g, stream) -> dict:
     """The configuration's full range: one enumeration to depth 8, timed
     once, and the 8-cliques of the stored 1/64 heaviest-first root sample
@@ -770,6 +809,7 @@ def main():
         line["learned_training"] = learned.info
         line["configs"] = {"er516": config_er516(stream), "rmat16": config_rmat16(stream, learned),
                            "ba4096": config_ba4096(stream), "sbm2000": config_sbm2000(stream, learned)}
+        line["balancing_ablation"] = balancing_ablation(stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, cores, _, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_stride)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

@@ -271,8 +271,7 @@ def test_schedule_never_changes_counts(cfg):
 def test_monitored_balancing_same_counts(threshold):
     """The paper's host-monitored stop / redistribute / restart balancing
     gives the in-kernel hand-off's counts, for cliques and motifs (and 5-
-    and 7-cliques with the deeper tails); at a high threshold the first
-    launch is stopped early and the spilled work relaunched."""
+    and 7-cliques with the deeper tails)."""
     g, ref_c, ref_m = _schedule_reference()
     dg = gpm.graph_from_csr(g)
     c6, st = gpm.gpm_count_monitored(dg, gpm.GPM_APP_CLIQUE, 6, threshold)
@@ -286,8 +285,19 @@ def test_monitored_balancing_same_counts(threshold):
     assert np.array_equal(m5, gpm.gpm_motif_count(dg, 5))
     if threshold == 0.0:
         assert st["launches"] == 1 and st["spilled_units"] == 0
-    if threshold == 0.9:
-        assert st["launches"] >= 2 and st["spilled_units"] > 0, st
+
+
+def test_monitored_balancing_redistributes():
+    """On the block-model workload (5-vertex motifs, 2,000 roots for a few
+    thousand warps, ~0.2 s of work) the monitor at the paper's motif
+    threshold stops the first launch while work is left, spills it and
+    relaunches; the counts equal the oracle's."""
+    g = G.workload("sbm2000")
+    dg = gpm.graph_from_csr(g)
+    m5, st = gpm.gpm_count_monitored(dg, gpm.GPM_APP_MOTIF, 5, 0.4)
+    assert st["launches"] >= 2 and st["spilled_units"] > 0, st
+    want = next(c["patterns"] for c in _golden("sbm2000_full")["cases"] if c["k"] == 5 and c["roots"] is None)
+    assert {str(gpm.gpm_motif_pattern(5, p)): int(x) for p, x in enumerate(m5) if x} == want
 
 
 # --------------------------------------------------------- invalid inputs
@@ -345,13 +355,15 @@ def _golden(name):
         return json.load(f)
 
 
-@pytest.mark.parametrize("name", ["er516", "sbm2000", "rmat16", "chunglu1m", "rmat16_full", "sbm2000_full"])
+@pytest.mark.parametrize("name", ["er516", "sbm2000", "rmat16", "chunglu1m", "rmat16_full", "sbm2000_full",
+                                  "rmat16_strat"])
 def test_workload_golden(name):
     """Full-size workloads, in the launch configuration the benchmark uses:
     full counts where the oracle finishes, else exact per-root counts on the
     seeded root samples stored beside them (the *_full files: every root, or
     the learned-scheduling comparison's 512 roots, by the oracle's ESU
-    route)."""
+    route; rmat16_strat: up to 16 roots per up-degree band at k = 5, 6, 7,
+    the heaviest the oracle finishes within its per-root limit)."""
     data = _golden(name)
     g = G.workload(data["workload"])
     assert g.sha256() == data["sha256"]
