@@ -227,6 +227,17 @@ gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
  *               whole loop's host time.
  * Same counts as gpm_clique_count / gpm_motif_count.  Errors as those.
  */
+/*
+ * The paper's DM_DFS baseline (Section 4.2; Table optimizations-performance),
+ * for comparison only: k-cliques (2 <= k <= 16) counted by one thread per
+ * root, depth first, with sorted candidate lists intersected by merges in a
+ * per-thread stack in device memory -- no warp cooperation, no bitmaps, no
+ * load balancing.  Same count as gpm_clique_count; its kernel time is in
+ * gpm_get_stats.  The stack takes (k-1) x (largest out-degree) ints per
+ * thread for 152 x 8 x 256 threads.  Errors as gpm_clique_count.
+ */
+gpm_status gpm_clique_count_dfs(gpm_graph* g, int k, uint64_t* out_count);
+
 typedef struct {
     int32_t launches;
     int32_t pad;

@@ -295,6 +295,16 @@ gpm_status gpm_count_roots(gpm_graph* g, int app, int k, const int32_t* roots, i
     });
 }
 
+gpm_status gpm_clique_count_dfs(gpm_graph* g, int k, uint64_t* out_count) {
+    return guarded([&] {
+        check_graph(g);
+        if (!out_count) fail(GPM_EINVAL, "out_count is NULL");
+        uint64_t c = 0;
+        run_clique_dfs(g, k, &c);
+        *out_count = c;
+    });
+}
+
 gpm_status gpm_count_monitored(gpm_graph* g, int app, int k, double threshold, uint64_t* counts, int64_t counts_len,
                                gpm_monitor_stats* stats) {
     return guarded([&] {

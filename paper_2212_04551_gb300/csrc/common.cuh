@@ -199,6 +199,7 @@ struct MonitorStats {
     double wall_ms = 0.0;     // the whole loop, host monitor included
 };
 void run_clique_monitored(gpm_graph* g, int k, double threshold, uint64_t* count_out, MonitorStats* ms);
+void run_clique_dfs(gpm_graph* g, int k, uint64_t* count_out);   // the paper's DM_DFS baseline
 void run_motif_monitored(gpm_graph* g, int k, double threshold, uint64_t* counts_out, MonitorStats* ms);
 
 // clique.cu / motif.cu

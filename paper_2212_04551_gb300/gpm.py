@@ -102,6 +102,7 @@ SIGNATURES = {
     "gpm_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_config)]),
     "gpm_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gpm_stats)]),
     "gpm_motif_count_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, _u64p, ctypes.c_int64, _vp]),
+    "gpm_clique_count_dfs": (ctypes.c_int, [_vp, ctypes.c_int, _u64p]),
     "gpm_count_monitored": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _u64p, ctypes.c_int64,
                                            ctypes.POINTER(gpm_monitor_stats)]),
     "gpm_selftest_sum": (ctypes.c_int, [_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _u64p]),
@@ -260,6 +261,13 @@ def gpm_count_roots(g: Graph, app: int, k: int, roots=None, per_root: bool = Fal
                                 pr.ctypes.data_as(_u64p) if pr is not None else None)
     _check(st, "gpm_count_roots")
     return counts, (pr[:nrep] if pr is not None else None)
+
+
+def gpm_clique_count_dfs(g: Graph, k: int) -> int:
+    """k-cliques by the paper's DM_DFS baseline (one thread per root)."""
+    out = ctypes.c_uint64()
+    _check(load().gpm_clique_count_dfs(g, int(k), ctypes.byref(out)), "gpm_clique_count_dfs")
+    return out.value
 
 
 def gpm_count_monitored(g: Graph, app: int, k: int, threshold: float):

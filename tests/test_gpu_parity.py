@@ -599,3 +599,15 @@ def test_motif_k8():
     lhs = sum(_dominating(8, gpm.gpm_motif_pattern(8, p)) * int(c) for p, c in enumerate(c8) if c)
     assert lhs == sum(comb(int(x), 7) for x in g.degrees())
     assert int(c8.sum()) > 0
+
+
+def test_dm_dfs_baseline_counts():
+    """The paper's DM_DFS baseline kernel (one thread per root, merged
+    sorted lists) against closed forms and the oracle."""
+    for n in (2, 9, 40):
+        dg = gpm.graph_from_csr(G.complete(n))
+        assert [gpm.gpm_clique_count_dfs(dg, k) for k in range(2, 7)] == [comb(n, k) for k in range(2, 7)]
+    for g in (G.gnp(120, 0.3, 81), G.sbm(500, 50, 0.5, 0.02, 82), G.turan(60, 6)):
+        dg = gpm.graph_from_csr(g)
+        for k in (3, 4, 5, 6):
+            assert gpm.gpm_clique_count_dfs(dg, k) == O.clique_count(g, k), (g.n, k)
