@@ -643,6 +643,9 @@ PROFILE_CASES = {
     # the headline kernel: every root, k = 4..6 (two-level tail) and the
     # 1/64 heaviest-first sample at k = 7 (compacted three-level tail)
     "clique_chunglu1m_k4_6": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_clique_count_range(dg, 4, 6)),
+    # the headline step itself (one launch of about 5 s: capture only a few
+    # sections of it)
+    "clique_chunglu1m_k4_7": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_clique_count_range(dg, 4, 7)),
     "clique_chunglu1m_k7_sample": ("chunglu1m", lambda gpm, g, dg: gpm.gpm_count_roots(
         dg, gpm.GPM_APP_CLIQUE, 7, heaviest_first(g)[0::64])[0]),
     # the bulk of the k = 7 search without its few heaviest roots (whose

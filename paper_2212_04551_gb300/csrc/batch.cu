@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     uint32_t* cq = reinterpret_cast<uint32_t*>(base);
     const CqLayout L = cq_layout(p.cq_maxd, p.cq_wmax, false);
     CliqueUnit* unit = reinterpret_cast<CliqueUnit*>(cq + L.unit);
-    CliqueWalk cw;
+    CliqueWalk cw{};
     cw.off = p.off;
     cw.adj = p.adj;
     cw.outdeg = p.outdeg;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     uint32_t* agg = reinterpret_cast<uint32_t*>(wc + ((p.npat + 1) & ~1));
     unsigned char* marks = reinterpret_cast<unsigned char*>(agg + ((p.agg_words + 3) & ~3));
     int32_t* slab = reinterpret_cast<int32_t*>(marks + p.mark_stride);
-    MotifWalk mw;
+    MotifWalk mw{};
     mw.indptr = p.indptr;
     mw.indices = p.indices;
     mw.lut = p.lut;
@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     mw.err = &p.ctl->error;
     mw.agg = p.agg_words > 0 ? agg : nullptr;
     mw.agg_min = p.agg_words > 0 ? p.agg_min : 0;
+    mw.monitor = false;
+    mw.spill = nullptr;
+    mw.spill_cap = 0;
     for (int v = lane; v < p.mark_stride; v += 32) marks[v] = 0;
     for (int j = lane; j < p.npat; j += 32) wc[j] = 0ull;
     __syncwarp();

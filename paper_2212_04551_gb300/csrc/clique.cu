@@ -91,7 +91,7 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
 
     for (int j = lane; j < CQ_LEVELS; j += 32) wcnt[j] = 0ull;
     __syncwarp();
-    CliqueWalk walk;
+    CliqueWalk walk{};
     walk.off = p.off;
     walk.adj = p.adj;
     walk.outdeg = p.outdeg;

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
 
     const long long gw = (long long)blockIdx.x * nwb + wib;
     Control* ctl = p.ctl;
-    MotifWalk a;
+    MotifWalk a{};
     a.indptr = p.indptr;
     a.indices = p.indices;
     a.lut = p.lut;
