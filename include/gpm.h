@@ -92,7 +92,10 @@ gpm_status gpm_graph_info(const gpm_graph* g, int32_t* n, int64_t* m, int32_t* m
  * GPM_CLIQUE_MAX_K.  k = 1 gives n and k = 2 gives m.  The enumeration runs on
  * the degree-ordered orientation of G (each clique is reached once, from its
  * lowest-(degree, id) vertex), which plays the role of the paper's "lower"
- * filter.  out_count: host pointer to one uint64.
+ * filter.  Roots with at most 1,024 out-neighbours are counted on bitmaps of
+ * their out-neighbourhood in shared memory; roots above that, in the same
+ * call, by sorted-list intersection (the paper's extension arrays) with
+ * per-warp lists in device memory.  out_count: host pointer to one uint64.
  * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT, GPM_EOVERFLOW.
  */
 gpm_status gpm_clique_count(gpm_graph* g, int k, uint64_t* out_count);
@@ -358,7 +361,8 @@ void gpm_batch_destroy(gpm_batch* b);
  * 3 <= motif_k <= 7.  The first call with a given (clique_k, motif_k) and
  * launch shape captures a CUDA graph; later calls replay it.
  * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_EOVERFLOW, GPM_ENOTIMPL (a
- * graph too large for the shared-memory state).
+ * graph too large for the shared-memory state, or, with clique_k > 0, an
+ * oriented out-degree above 1,024: the batched kernel has no list path).
  */
 gpm_status gpm_batch_count(gpm_batch* b, int clique_k, int motif_k, uint64_t* clique_counts, uint64_t* motif_counts);
 

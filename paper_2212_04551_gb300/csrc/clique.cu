@@ -225,8 +225,10 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
         const int r = p.roots[root_pos];
         const int d = p.outdeg[r];
         unsigned long long unit_sum = 0;   // lane-private k_hi-cliques of this unit
-        const bool ok = p.donate ? cq_walk<true>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane)
-                                 : cq_walk<false>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane);
+        // a root above the bitmap limit (and its seeds) is the list path's
+        const bool ok = d > p.maxd ? true
+                        : p.donate ? cq_walk<true>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane)
+                                   : cq_walk<false>(walk, unit, root_pos, r, d, cached_root, unit_sum, top_km1, wops, lane);
         if (!ok) aborted = true;
         top_sum = gpm_add_cc(top_sum, unit_sum, ovf);
         if (p.per_root) {
@@ -311,9 +313,6 @@ struct CliqueLaunch {
 
 static CliqueLaunch plan_clique_launch(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_counter,
                                        unsigned long long n_seed, unsigned long long extra_units) {
-    if (g->max_outdeg > CQ_MAX_OUTDEG)
-        fail(GPM_ENOTIMPL, "oriented out-degree " + std::to_string(g->max_outdeg) + " exceeds the bitmap limit of " +
-                               std::to_string(CQ_MAX_OUTDEG));
     CliqueLaunch c;
     CliqueParams& p = c.p;
     cudaStream_t s = g->stream;
@@ -325,7 +324,8 @@ static CliqueLaunch plan_clique_launch(gpm_graph* g, int k_lo, int k_hi, const i
     p.n_roots = n_counter;
     p.k_lo = std::max(k_lo, 3);
     p.k_hi = k_hi;
-    p.maxd = std::max(g->max_outdeg, 1);
+    // roots above the bitmap limit are left to the list path (clique_list.cu)
+    p.maxd = std::min(std::max(g->max_outdeg, 1), CQ_MAX_OUTDEG);
     p.wmax = (p.maxd + 31) / 32;
     p.compact = g->cfg.clique_compact;   // before the layout: it sizes the compaction region
     // the compacted three-level tail runs where the three-level tail does
@@ -420,6 +420,7 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
         GPM_CUDA(cudaEventRecord(g->ev0, s));
         k_clique<<<L.gr.blocks, L.wpb * 32, L.smem, s>>>(p);
         GPM_CUDA(cudaGetLastError());
+        run_clique_list(g, k_lo, k_hi, d_roots, n_roots, d_per_root, ctl, CQ_MAX_OUTDEG);
         GPM_CUDA(cudaEventRecord(g->ev1, s));
         st.grid_blocks = L.gr.blocks;
         st.warps_per_block = L.wpb;
@@ -437,6 +438,7 @@ void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_
     st.word_ops = h.word_ops;
     st.busy_warp_ns = h.busy_ns;
     st.kernel_launches = st.grid_blocks ? (n_split > 0 ? 3 : 2) : (k_hi <= 2 && n_roots > 0 ? 1 : 0);
+    if (st.grid_blocks && g->max_outdeg > CQ_MAX_OUTDEG) st.kernel_launches += 2;   // the list path
     g->stats = st;
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");
     if (h.error) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
@@ -486,6 +488,22 @@ void run_clique_monitored(gpm_graph* g, int k, double threshold, uint64_t* count
             st.units_done += h.units_done;
         };
         ms = monitored_loop(g, ctl, L.gr.total_warps(), n_roots, threshold, cap, launch, after);
+        if (g->max_outdeg > CQ_MAX_OUTDEG) {
+            // roots above the bitmap limit: the list path, in one more launch
+            Control h{};
+            GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
+            GPM_CUDA(cudaEventRecord(g->ev0, s));
+            run_clique_list(g, k, k, d_roots, n_roots, nullptr, ctl, CQ_MAX_OUTDEG);
+            GPM_CUDA(cudaEventRecord(g->ev1, s));
+            GPM_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+            GPM_CUDA(cudaStreamSynchronize(s));
+            float lms = 0.f;
+            GPM_CUDA(cudaEventElapsedTime(&lms, g->ev0, g->ev1));
+            if (h.overflow) fail(GPM_EOVERFLOW, "clique count exceeds 2^64-1");
+            total += h.counts[k];
+            ms.kernel_ms += lms;
+            ms.launches += 2;
+        }
         st.grid_blocks = L.gr.blocks;
         st.warps_per_block = L.wpb;
         st.kernel_ms = ms.kernel_ms;

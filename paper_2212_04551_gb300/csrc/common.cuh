@@ -149,6 +149,9 @@ struct alignas(128) Control {
     int overflow;
     int pad;
     alignas(128) unsigned long long counts[GPM_CLIQUE_MAX_K + 1];  // per clique size (clique kernel)
+    alignas(128) unsigned long long heavy_next;   // clique list path: next (heavy root, chunk) unit
+    int n_heavy;                                  // clique list path: roots above the bitmap limit
+    int pad_heavy;
 };
 
 // Device-side status values (mirrors gpm_status).
@@ -200,6 +203,10 @@ struct MonitorStats {
 };
 void run_clique_monitored(gpm_graph* g, int k, double threshold, uint64_t* count_out, MonitorStats* ms);
 void run_clique_dfs(gpm_graph* g, int k, uint64_t* count_out);   // the paper's DM_DFS baseline
+// clique_list.cu: roots whose out-degree exceeds the bitmap limit, counted
+// by list intersection after the bitmap launch (same Control, same counters)
+void run_clique_list(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
+                     unsigned long long* d_per_root, Control* ctl, int bitmap_limit);
 void run_motif_monitored(gpm_graph* g, int k, double threshold, uint64_t* counts_out, MonitorStats* ms);
 
 // clique.cu / motif.cu

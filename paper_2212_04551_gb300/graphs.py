@@ -104,6 +104,16 @@ def disjoint_union(*gs: CSR) -> CSR:
     return from_edges(off, np.concatenate(us), np.concatenate(vs))
 
 
+def join(a: CSR, b: CSR) -> CSR:
+    """The join a + b: a and b side by side (b's vertices shifted by a.n),
+    plus every edge between a vertex of a and a vertex of b."""
+    ea, eb = a.edges(), b.edges()
+    ia = np.repeat(np.arange(a.n, dtype=np.int64), b.n)
+    ib = np.tile(np.arange(b.n, dtype=np.int64), a.n) + a.n
+    return from_edges(a.n + b.n, np.concatenate([ea[:, 0], eb[:, 0] + a.n, ia]),
+                      np.concatenate([ea[:, 1], eb[:, 1] + a.n, ib]))
+
+
 # ---------------------------------------------------------------- structured
 
 def empty(n: int) -> CSR:

@@ -502,6 +502,36 @@ def test_bits_route_vs_networkx_per_root(seed):
 
 
 @pytest.mark.parametrize("seed", range(3))
+def test_clique_routes_on_joins(seed):
+    """The join a + b (all edges between a and b added): every clique of it
+    is a clique of a beside a clique of b, so its k-cliques number
+    sum_i c_i(a) c_{k-i}(b) with c_0 = 1.  The parts' counts come from
+    networkx; both clique routes must give the join's."""
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(900 + seed)
+    a = G.gnp(int(rng.integers(8, 30)), float(rng.uniform(0.1, 0.6)), 910 + seed)
+    b = G.gnp(int(rng.integers(5, 25)), float(rng.uniform(0.1, 0.6)), 920 + seed)
+    k_hi = 7
+
+    def nx_counts(g):
+        h = nx.Graph()
+        h.add_nodes_from(range(g.n))
+        h.add_edges_from(map(tuple, g.edges()))
+        c = [1] + [0] * k_hi
+        for q in nx.enumerate_all_cliques(h):
+            if len(q) <= k_hi:
+                c[len(q)] += 1
+        return c
+
+    ca, cb = nx_counts(a), nx_counts(b)
+    want = [sum(ca[i] * cb[k - i] for i in range(k + 1)) for k in range(k_hi + 1)]
+    j = G.join(a, b)
+    assert O.clique_count_bits(j, k_hi)[1:] == want[1:]
+    for k in (3, 5, 7):
+        assert O.clique_count(j, k) == want[k]
+
+
+@pytest.mark.parametrize("seed", range(3))
 def test_bits_route_vs_list_route_wide_rows(seed):
     """Out-neighbourhoods of 60-200 vertices (rows of 1-4 words): the same
     per-root counts as the sorted-list route of Algorithm 4 in the (degree,
