@@ -241,6 +241,41 @@ gpm_status gpm_get_stats(const gpm_graph* g, gpm_stats* out);
  */
 gpm_status gpm_clique_count_dfs(gpm_graph* g, int k, uint64_t* out_count);
 
+/*
+ * Subgraph listing with an asynchronous host consumer (aggregate_store,
+ * Section 4.3.4: found k-vertex subgraphs go to a buffer that the CPU
+ * consumes while the GPU keeps producing).  The kernel appends one record
+ * per subgraph to a ring in mapped (pinned) host memory; the calling thread
+ * takes the records in order while the kernel runs and hands them to
+ * `consumer` in batches.
+ *   app, k       : GPM_APP_CLIQUE, 3 <= k <= 16: every k-clique; or
+ *                  GPM_APP_MOTIF, 3 <= k <= 8: every connected induced
+ *                  k-vertex subgraph.
+ *   pattern      : -1 for every subgraph; for motifs, a pattern id (see
+ *                  gpm_motif_pattern) to list only that pattern's subgraphs
+ *                  (subgraph querying).  Cliques take -1 only.
+ *   ring_records : ring capacity in records, >= 64 (0: 65,536).
+ *   consumer     : called on the calling thread with `count` records of
+ *                  `record_words` = k + 1 int32 each: the k vertex ids
+ *                  (cliques: in (degree, id) order from the clique's first
+ *                  vertex; motifs: in traversal order from the smallest id),
+ *                  then the pattern id (motifs) or -1 (cliques).  The array
+ *                  is valid during the call only.  Return 0 to go on, any
+ *                  other value to stop the listing (the call then returns
+ *                  GPM_OK with fewer records than exist).
+ *   user         : passed through to consumer.
+ *   delivered    : nullable; records handed to consumer.
+ * Every subgraph is listed exactly once (the same sets gpm_clique_count /
+ * gpm_motif_count count), in no particular order.  Kernel time is in
+ * gpm_get_stats.  If the ring stays full for longer than max_idle_ms
+ * (the consumer does not keep up), the device gives up: GPM_ETIMEOUT, with
+ * the records delivered so far.
+ * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT.
+ */
+typedef int32_t (*gpm_list_consumer)(const int32_t* records, int64_t count, int32_t record_words, void* user);
+gpm_status gpm_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_records, gpm_list_consumer consumer,
+                    void* user, uint64_t* delivered);
+
 typedef struct {
     int32_t launches;
     int32_t pad;

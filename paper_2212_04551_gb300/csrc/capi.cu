@@ -305,6 +305,15 @@ gpm_status gpm_clique_count_dfs(gpm_graph* g, int k, uint64_t* out_count) {
     });
 }
 
+gpm_status gpm_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_records, gpm_list_consumer consumer,
+                    void* user, uint64_t* delivered) {
+    if (delivered) *delivered = 0;
+    return guarded([&] {
+        check_graph(g);
+        run_list(g, app, k, pattern, ring_records, consumer, user, delivered);
+    });
+}
+
 gpm_status gpm_count_monitored(gpm_graph* g, int app, int k, double threshold, uint64_t* counts, int64_t counts_len,
                                gpm_monitor_stats* stats) {
     return guarded([&] {

@@ -29,6 +29,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "list_ring.cuh"
 
 namespace gpm {
 
@@ -244,6 +245,152 @@ void run_clique_list(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, i
     GPM_CUDA(cudaGetLastError());
     k_clique_list<<<(int)blocks, CL_WARPS * 32, 0, s>>>(p);
     GPM_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Listing (aggregate_store): every k-clique as a record of its k vertex ids
+// in orientation order (root first), appended to the host ring
+// (list_ring.cuh).  The same list-form search over every root: a traversal
+// of size k-1 hands each of its candidates to the ring instead of counting
+// them.  Units are (root, quarter of its children by the work model).
+
+constexpr int CS_CHUNKS = 4;
+
+struct StoreParams {
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ adj;
+    const int32_t* __restrict__ outdeg;
+    const int32_t* __restrict__ roots;
+    long long n_roots;
+    int k;
+    int maxd;
+    int32_t* stack;        // per warp: k - 2 slots of maxd ids
+    Control* ctl;
+    ListRing ring;
+};
+
+// append the candidates C[0 .. c-1] of the traversal tr[0 .. np-1]
+__device__ __forceinline__ bool cs_emit_all(const StoreParams& p, unsigned long long& tail_seen, const int* tr, int np,
+                                            const int32_t* C, int c, int lane) {
+    for (int base = 0; base < c; base += 32) {
+        const bool act = base + lane < c;
+        const int x = act ? C[base + lane] : 0;
+        if (!lr_emit(p.ring, tail_seen, tr, np, -1, x, -1, act, lane)) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(CL_WARPS * 32) k_clique_store(StoreParams p) {
+    __shared__ int s_tr[CL_WARPS][GPM_CLIQUE_MAX_K + 1];
+    __shared__ int s_pos[CL_WARPS][GPM_CLIQUE_MAX_K + 1];
+    __shared__ int s_len[CL_WARPS][GPM_CLIQUE_MAX_K + 1];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int* tr = s_tr[wib];
+    int* pos = s_pos[wib];
+    int* len = s_len[wib];
+    const long long gw = blockIdx.x * (long long)CL_WARPS + wib;
+    int32_t* const st = p.stack + gw * (long long)max(p.k - 2, 1) * p.maxd;
+    const unsigned long long n_units = (unsigned long long)p.n_roots * CS_CHUNKS;
+    Control* ctl = p.ctl;
+    unsigned long long tail_seen = 0;   // lane 0
+    bool live = true;
+    while (live) {
+        unsigned long long u = 0;
+        int err = 0;
+        if (lane == 0) {
+            u = atomicAdd(&ctl->next_root, 1ull);
+            err = *(volatile int*)&ctl->error;
+        }
+        u = __shfl_sync(GPM_FULL_MASK, u, 0);
+        if (__shfl_sync(GPM_FULL_MASK, err, 0) || u >= n_units) break;
+        const long long t = (long long)(u / CS_CHUNKS);
+        const int chunk = (int)(u % CS_CHUNKS);
+        const int r = p.roots[t];
+        const int d = p.outdeg[r];
+        const int lo = gpm_balanced_cut(d, chunk, CS_CHUNKS, p.k);
+        const int hi = gpm_balanced_cut(d, chunk + 1, CS_CHUNKS, p.k);
+        const int32_t* Nr = p.adj + p.off[r];
+        for (int i = lo; i < hi && live; i++) {
+            const int v = Nr[i];
+            __syncwarp();
+            if (lane == 0) {
+                tr[0] = r;
+                tr[1] = v;
+            }
+            const int c2 = cl_intersect(Nr, d, p.adj + p.off[v], p.outdeg[v], st, lane);   // syncs the warp
+            if (p.k == 3) {
+                live = cs_emit_all(p, tail_seen, tr, 2, st, c2, lane);
+                continue;
+            }
+            if (c2 == 0) continue;
+            // depth first: the traversal of size s has its list in slot s - 2
+            int s = 2;
+            if (lane == 0) {
+                pos[2] = 0;
+                len[2] = c2;
+            }
+            __syncwarp();
+            while (s >= 2 && live) {
+                const int ps = pos[s], ls = len[s];
+                if (ps >= ls) {
+                    s--;
+                    continue;
+                }
+                const int32_t* C = st + (long long)(s - 2) * p.maxd;
+                const int w = C[ps];
+                __syncwarp();
+                if (lane == 0) {
+                    pos[s] = ps + 1;
+                    tr[s] = w;
+                }
+                int32_t* Cw = st + (long long)(s - 1) * p.maxd;
+                const int cw = cl_intersect(C, ls, p.adj + p.off[w], p.outdeg[w], Cw, lane);
+                if (s + 2 == p.k) {   // tr[0 .. s] is a (k-1)-clique: each candidate completes one
+                    live = cs_emit_all(p, tail_seen, tr, s + 1, Cw, cw, lane);
+                    continue;
+                }
+                if (cw == 0) continue;
+                s++;
+                if (lane == 0) {
+                    pos[s] = 0;
+                    len[s] = cw;
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+void launch_clique_store(gpm_graph* g, int k, const ListRing& ring, Control* ctl) {
+    ensure_dag(g);
+    cudaStream_t s = g->stream;
+    const int32_t* d_roots = ensure_root_order(g, GPM_APP_CLIQUE);
+    const int maxd = std::max(g->max_outdeg, 1);
+    const size_t per_warp = sizeof(int32_t) * (size_t)std::max(k - 2, 1) * (size_t)maxd;
+    const size_t budget = size_t(1) << 30;
+    long long blocks = (long long)g->num_sms * 8;
+    blocks = std::min<long long>(blocks, std::max<long long>(1, (long long)(budget / (per_warp * CL_WARPS))));
+    g->scratch_slab.ensure(per_warp * CL_WARPS * (size_t)blocks);
+    StoreParams p{};
+    p.off = g->dag_off.as<int32_t>();
+    p.adj = g->dag_adj.as<int32_t>();
+    p.outdeg = g->dag_outdeg.as<int32_t>();
+    p.roots = d_roots;
+    p.n_roots = g->n;
+    p.k = k;
+    p.maxd = maxd;
+    p.stack = g->scratch_slab.as<int32_t>();
+    p.ctl = ctl;
+    p.ring = ring;
+    GPM_CUDA(cudaEventRecord(g->ev0, s));
+    if (g->n > 0) k_clique_store<<<(int)blocks, CL_WARPS * 32, 0, s>>>(p);
+    GPM_CUDA(cudaGetLastError());
+    GPM_CUDA(cudaEventRecord(g->ev1, s));
+    g->stats = gpm_stats{};
+    g->stats.grid_blocks = (int)blocks;
+    g->stats.warps_per_block = CL_WARPS;
+    g->stats.kernel_launches = g->n > 0 ? 1 : 0;
 }
 
 }  // namespace gpm

@@ -216,10 +216,21 @@ void run_motif_monitored(gpm_graph* g, int k, double threshold, uint64_t* counts
 void run_clique(gpm_graph* g, int k_lo, int k_hi, const int32_t* d_roots, int64_t n_roots,
                 unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
                 const SplitPlan* plan = nullptr);
+struct ListJob;
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter = -1,
                const SplitPlan* plan = nullptr, double monitor_threshold = -1.0,
-               MonitorStats* monitor_stats = nullptr);
+               MonitorStats* monitor_stats = nullptr, ListJob* list = nullptr);
+
+// Listing (aggregate_store; list.cu, list_ring.cuh).  list_drain runs the
+// host consumer until the launch recorded before g->ev1 has ended and its
+// records are taken; list_ring_of is the device view of the job's ring.
+struct ListRing;
+ListRing list_ring_of(const ListJob* job, Control* ctl);
+void list_drain(ListJob* job, gpm_graph* g, Control* ctl);
+void launch_clique_store(gpm_graph* g, int k, const ListRing& ring, Control* ctl);
+void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_records, gpm_list_consumer consumer,
+              void* user, uint64_t* delivered);
 
 // sched.cu
 void root_features(gpm_graph* g, int k, float* d_out);

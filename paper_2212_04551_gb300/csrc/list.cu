@@ -1,0 +1,194 @@
+// list.cu -- subgraph listing with an asynchronous host consumer
+// (aggregate_store, Section 4.3.4), host side.
+//
+// The ring of records lives in mapped pinned host memory: the kernel writes
+// records straight into it and this thread takes them, in order, while the
+// kernel runs (list_ring.cuh has the record format and the device side).
+// The consumer sees each batch once; the slots are given back to the device
+// before the consumer runs, so production and consumption overlap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "list_ring.cuh"
+
+namespace gpm {
+
+struct ListJob {
+    int k = 0;
+    int stride = 0;                        // words per record: sequence + k ids + tag
+    unsigned long long cap = 0;            // records
+    int32_t* host_rec = nullptr;           // mapped pinned ring
+    int32_t* dev_rec = nullptr;
+    unsigned long long* host_tail = nullptr;   // mapped pinned: records consumed
+    unsigned long long* dev_tail = nullptr;
+    DevBuf head;                           // device: records reserved
+    int tag_filter = -1;
+    unsigned long long max_wait_ns = 0;
+    gpm_list_consumer consumer = nullptr;
+    void* user = nullptr;
+    uint64_t delivered = 0;
+    bool stopped = false;
+    cudaStream_t stream = nullptr;         // the launch's stream
+    bool launched = false;
+
+    ~ListJob() {
+        // the kernel may still run after an error on the host side: its waits
+        // are bounded, so wait for it before the ring goes away
+        if (launched) cudaStreamSynchronize(stream);
+        if (host_rec) cudaFreeHost(host_rec);
+        if (host_tail) cudaFreeHost(host_tail);
+    }
+};
+
+ListRing list_ring_of(const ListJob* j, Control* ctl) {
+    ListRing r{};
+    r.rec = j->dev_rec;
+    r.cap = j->cap;
+    r.stride = j->stride;
+    r.head = j->head.as<unsigned long long>();
+    r.tail = j->dev_tail;
+    r.ctl = ctl;
+    r.max_wait_ns = j->max_wait_ns;
+    r.tag_filter = j->tag_filter;
+    return r;
+}
+
+// Take the records of the launch that ends at g->ev1, in order, until it has
+// ended and everything it reserved is taken (or the listing stopped / failed).
+void list_drain(ListJob* j, gpm_graph* g, Control* ctl) {
+    cudaStream_t side = nullptr;
+    GPM_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } guard{side};
+    const int words = j->stride - 1;
+    const unsigned long long batch = std::min<unsigned long long>(j->cap, 65536);
+    std::vector<int32_t> staging((size_t)batch * words);
+    unsigned long long tail = 0;
+    bool ended = false;
+    unsigned long long head_end = 0;
+    int idle_polls = 0;
+    for (;;) {
+        unsigned long long n = 0;
+        if (!j->stopped) {
+            while (n < batch) {
+                const unsigned long long q = tail + n;
+                const int32_t* rec = j->host_rec + (size_t)(q % j->cap) * j->stride;
+                const uint32_t seq = __atomic_load_n(reinterpret_cast<const uint32_t*>(rec), __ATOMIC_ACQUIRE);
+                if (seq != (uint32_t)(q + 1)) break;
+                std::memcpy(staging.data() + (size_t)n * words, rec + 1, sizeof(int32_t) * words);
+                n++;
+            }
+        }
+        if (n) {
+            idle_polls = 0;
+            tail += n;
+            __atomic_store_n(j->host_tail, tail, __ATOMIC_RELEASE);   // the slots are free again
+            j->delivered += n;
+            if (j->consumer(staging.data(), (int64_t)n, (int32_t)words, j->user) != 0 && !j->stopped) {
+                j->stopped = true;
+                const int stop = DEV_STOPPED;
+                GPM_CUDA(cudaMemcpyAsync(&ctl->error, &stop, sizeof(int), cudaMemcpyHostToDevice, side));
+                GPM_CUDA(cudaStreamSynchronize(side));
+            }
+            continue;
+        }
+        if (ended) {
+            if (tail < head_end)
+                fail(GPM_ECUDA, "listing ended with " + std::to_string(head_end - tail) + " records unwritten");
+            break;
+        }
+        const cudaError_t q = cudaEventQuery(g->ev1);
+        if (q == cudaSuccess) {
+            int err = 0;
+            GPM_CUDA(cudaMemcpyAsync(&head_end, j->head.ptr, sizeof(head_end), cudaMemcpyDeviceToHost, side));
+            GPM_CUDA(cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, side));
+            GPM_CUDA(cudaStreamSynchronize(side));
+            if (j->stopped || err) break;   // an aborted launch leaves reserved records unwritten
+            ended = true;                   // everything reserved is written: take the rest
+            continue;
+        }
+        if (q != cudaErrorNotReady) check_cuda(q, "cudaEventQuery");
+        // nothing ready: spin briefly, then back off
+        if (++idle_polls > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_records, gpm_list_consumer consumer,
+              void* user, uint64_t* delivered) {
+    if (delivered) *delivered = 0;
+    if (!consumer) fail(GPM_EINVAL, "consumer is NULL");
+    if (app == GPM_APP_CLIQUE) {
+        if (k < 3 || k > GPM_CLIQUE_MAX_K) fail(GPM_EINVAL, "clique listing needs 3 <= k <= 16");
+        if (pattern != -1) fail(GPM_EINVAL, "clique listing takes pattern -1");
+    } else if (app == GPM_APP_MOTIF) {
+        if (k < 3 || k > GPM_MOTIF_MAX_K) fail(GPM_EINVAL, "motif listing needs 3 <= k <= 8");
+        if (pattern < -1 || pattern >= pattern_table(k).num_patterns) fail(GPM_EINVAL, "pattern id out of range");
+    } else {
+        fail(GPM_EINVAL, "unknown app");
+    }
+    if (ring_records == 0) ring_records = 65536;
+    if (ring_records < 64 || ring_records > (int64_t(1) << 30)) fail(GPM_EINVAL, "ring_records out of range [64, 2^30]");
+    ListJob j;
+    // the count delivered so far is reported on every way out, errors included
+    struct Report {
+        const ListJob& j;
+        uint64_t* out;
+        ~Report() {
+            if (out) *out = j.delivered;
+        }
+    } report{j, delivered};
+    j.stream = g->stream;
+    j.k = k;
+    j.stride = k + 2;
+    j.cap = (unsigned long long)ring_records;
+    j.tag_filter = pattern;
+    j.max_wait_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
+    j.consumer = consumer;
+    j.user = user;
+    const size_t ring_bytes = sizeof(int32_t) * (size_t)j.cap * j.stride;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&j.host_rec), ring_bytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&j.host_tail), 64, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        fail(GPM_ENOMEM, "mapped host ring of " + std::to_string(ring_bytes) + " bytes");
+    }
+    std::memset(j.host_rec, 0, ring_bytes);
+    std::memset(j.host_tail, 0, 64);
+    GPM_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&j.dev_rec), j.host_rec, 0));
+    GPM_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&j.dev_tail), j.host_tail, 0));
+    j.head.ensure(sizeof(unsigned long long));
+    cudaStream_t s = g->stream;
+    GPM_CUDA(cudaMemsetAsync(j.head.ptr, 0, sizeof(unsigned long long), s));
+    j.launched = true;
+
+    if (app == GPM_APP_MOTIF) {
+        std::vector<uint64_t> unused((size_t)pattern_table(k).num_patterns, 0);
+        run_motif(g, k, nullptr, 0, nullptr, unused.data(), -1, nullptr, -1.0, nullptr, &j);
+    } else {
+        g->scratch_small.ensure(sizeof(Control));
+        Control* ctl = g->scratch_small.as<Control>();
+        Control h{};
+        GPM_CUDA(cudaMemcpyAsync(ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
+        launch_clique_store(g, k, list_ring_of(&j, ctl), ctl);
+        list_drain(&j, g, ctl);
+        GPM_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+        GPM_CUDA(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        GPM_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+        g->stats.kernel_ms = ms;
+        if (h.error == DEV_ETIMEOUT)
+            fail(GPM_ETIMEOUT, "the ring stayed full for longer than max_idle_ms (" + std::to_string(j.delivered) +
+                                   " records delivered)");
+        if (h.error && h.error != DEV_STOPPED) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
+    }
+}
+
+}  // namespace gpm

@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "monitor.cuh"
 #include "motif_dev.cuh"
+#include "list_ring.cuh"
 
 namespace gpm {
 
@@ -56,11 +57,13 @@ struct MotifParams {
     int monitor;                // host-monitored balancing (no donation): count active warps, obey stop
     MotifUnit* spill;
     unsigned long long spill_cap;
+    ListRing list;              // LIST: the host ring the leaves go to
 };
 
 // GCOUNT: count patterns straight into the global counters (k = 8) instead
-// of per-block shared ones
-template <bool SMEM_STATE, bool GCOUNT>
+// of per-block shared ones.  LIST: hand every leaf to the host ring as a
+// record instead of counting it (listing; donation on, class-counted tail off).
+template <bool SMEM_STATE, bool GCOUNT, bool LIST = false>
 __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     MtWarp* W = reinterpret_cast<MtWarp*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT) + wib;
     uint32_t* agg = reinterpret_cast<uint32_t*>(smem_raw + sizeof(unsigned long long) * MT_MAXPAT + sizeof(MtWarp) * nwb) +
                     (size_t)wib * p.agg_words;
-    if (!GCOUNT)
+    if (!GCOUNT && !LIST)
         for (int j = threadIdx.x; j < p.npat; j += blockDim.x) bcnt[j] = 0ull;
 
     const long long gw = (long long)blockIdx.x * nwb + wib;
@@ -108,8 +111,17 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
         a.slab = p.slab + gw * p.slab_ints;
     }
     __syncthreads();
-    using Sink = typename std::conditional<GCOUNT, GlobalSink, BlockSink>::type;
-    Sink sink{GCOUNT ? p.counts : bcnt, &ctl->overflow};
+    using CountSink = typename std::conditional<GCOUNT, GlobalSink, BlockSink>::type;
+    using Sink = typename std::conditional<LIST, ListSink, CountSink>::type;
+    Sink sink{};
+    if constexpr (LIST) {
+        sink.ring = p.list;
+        sink.tail_seen = 0;
+        sink.err = &ctl->error;
+    } else {
+        sink.c = GCOUNT ? p.counts : bcnt;
+        sink.ovf = &ctl->overflow;
+    }
     const int32_t* __restrict__ indptr = p.indptr;
     const int32_t* __restrict__ indices = p.indices;
 
@@ -249,7 +261,7 @@ __global__ void __launch_bounds__(512, 2) k_motif(MotifParams p) {
     if (lane == 0) atomicAdd(&ctl->busy_ns, busy);
     if (lane == 0 && scanned) atomicAdd(&ctl->word_ops, scanned);
     __syncthreads();
-    if (!GCOUNT)
+    if (!GCOUNT && !LIST)
         for (int j = threadIdx.x; j < p.npat; j += blockDim.x) gpm_atomic_add_cc(&p.counts[j], bcnt[j], &ctl->overflow);
 }
 
@@ -290,8 +302,10 @@ __global__ void k_motif_seed(const int32_t* __restrict__ roots, long long n_coun
 
 void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
                unsigned long long* d_per_root, uint64_t* counts_out, int64_t n_counter, const SplitPlan* plan,
-               double monitor_threshold, MonitorStats* monitor_stats) {
+               double monitor_threshold, MonitorStats* monitor_stats, ListJob* list) {
     const bool monitored = monitor_threshold >= 0.0;
+    if (list && (monitored || k < 3 || d_roots || plan || d_per_root))
+        fail(GPM_EINVAL, "listing runs over every root, k >= 3, without schedules");
     if (k < 1 || k > MT_MAXK) fail(GPM_ENOTIMPL, "motif size k=" + std::to_string(k) + " not built");
     const PatternTable& tab = pattern_table(k);
     const int npat = (int)tab.num_patterns;
@@ -373,7 +387,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     const size_t fixed_smem = sizeof(unsigned long long) * MT_MAXPAT + 16;
     // the class-counted tail needs two free mark bits at level k-2: k <= 7
     const bool gcount = npat > MT_MAXPAT;
-    p.agg_min = k <= 7 ? g->cfg.motif_agg_min : 0;
+    p.agg_min = k <= 7 && !list ? g->cfg.motif_agg_min : 0;
     p.agg_words = p.agg_min > 0 ? mt_agg_words(k) : 0;
     const size_t agg_bytes = sizeof(uint32_t) * (size_t)p.agg_words;
     const bool smem_state =
@@ -403,8 +417,9 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     }
     const size_t base_smem = sizeof(unsigned long long) * MT_MAXPAT + (sizeof(MtWarp) + agg_bytes) * wpb + 16;
     const size_t smem = base_smem + (smem_state ? (size_t)wpb * p.smem_warp_bytes : 0);
-    const void* kfun = smem_state ? (gcount ? (const void*)k_motif<true, true> : (const void*)k_motif<true, false>)
-                                  : (gcount ? (const void*)k_motif<false, true> : (const void*)k_motif<false, false>);
+    const void* kfun = list ? (smem_state ? (const void*)k_motif<true, true, true> : (const void*)k_motif<false, true, true>)
+                       : smem_state ? (gcount ? (const void*)k_motif<true, true> : (const void*)k_motif<true, false>)
+                                    : (gcount ? (const void*)k_motif<false, true> : (const void*)k_motif<false, false>);
     GPM_CUDA(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     Grid gr = plan_grid(g, kfun, wpb, smem, max_per_sm);
     const long long nw = gr.total_warps();
@@ -435,7 +450,8 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
 
     // idle ring (capacity: a power of two >= every warp), mailboxes, seeds
     // (monitored: two spill buffers of one unit per level per warp instead)
-    p.donate = monitored ? 0 : g->cfg.donate;
+    // (listing: always with hand-offs, whose checks also notice a stop)
+    p.donate = monitored ? 0 : (list ? 1 : g->cfg.donate);
     unsigned long long cap = 1;
     while (cap < (unsigned long long)nw) cap <<= 1;
     const unsigned long long spill_cap = monitored ? (unsigned long long)nw * (MT_MAXK + 1) : 0ull;
@@ -464,9 +480,13 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
     p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
 
+    if (list) p.list = list_ring_of(list, ctl);
     auto launch_kernel = [&](const MotifParams& q) {
         GPM_CUDA(cudaEventRecord(g->ev0, s));
-        if (smem_state) {
+        if (list) {
+            if (smem_state) k_motif<true, true, true><<<gr.blocks, wpb * 32, smem, s>>>(q);
+            else k_motif<false, true, true><<<gr.blocks, wpb * 32, smem, s>>>(q);
+        } else if (smem_state) {
             if (gcount) k_motif<true, true><<<gr.blocks, wpb * 32, smem, s>>>(q);
             else k_motif<true, false><<<gr.blocks, wpb * 32, smem, s>>>(q);
         } else {
@@ -513,6 +533,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
         launch_kernel(p);
         st.grid_blocks = gr.blocks;
         st.warps_per_block = wpb;
+        if (list) list_drain(list, g, ctl);
     }
     GPM_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
     GPM_CUDA(cudaMemcpyAsync(host.data(), p.counts, sizeof(unsigned long long) * npat, cudaMemcpyDeviceToHost, s));
@@ -530,6 +551,9 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     st.kernel_launches = st.grid_blocks ? (n_split > 0 ? 3 : 2) : 0;
     g->stats = st;
     if (h.error) g->mark_bytes_cleared = 0;   // an aborted walk leaves marks behind
+    if (list && h.error == DEV_STOPPED) return;   // the consumer asked to stop
+    if (list && h.error == DEV_ETIMEOUT)
+        fail(GPM_ETIMEOUT, "the listing ring stayed full (or an idle warp waited) for longer than max_idle_ms");
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");
     if (h.error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
     if (h.error >= DEV_ECHECK) fail(GPM_ECUDA, "device consistency check " + std::to_string(h.error - DEV_ECHECK) + " failed");

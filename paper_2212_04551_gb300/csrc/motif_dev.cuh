@@ -27,6 +27,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "list_ring.cuh"
 
 namespace gpm {
 
@@ -108,6 +109,7 @@ __device__ __forceinline__ int mt_code_off(int i) { return i * (i - 1) / 2 - 1; 
 // Shared counters of one block (single-graph kernel); ovf: the launch's
 // overflow flag, raised if a counter wraps.
 struct BlockSink {
+    static constexpr bool kList = false;
     unsigned long long* c;
     int* ovf;
     __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }
@@ -116,6 +118,7 @@ struct BlockSink {
 // The launch's global counters (k = 8: 11,117 patterns do not fit a block's
 // shared memory).
 struct GlobalSink {
+    static constexpr bool kList = false;
     unsigned long long* c;
     int* ovf;
     __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }
@@ -123,9 +126,21 @@ struct GlobalSink {
 
 // Per-warp counters of the current unit (batched kernel), flushed per unit.
 struct WarpSink {
+    static constexpr bool kList = false;
     unsigned long long* c;
     int* ovf;
     __device__ __forceinline__ void add(int pid, unsigned long long v) { gpm_atomic_add_cc(&c[pid], v, ovf); }
+};
+
+// Listing (aggregate_store): every leaf becomes a record in the host ring
+// (list_ring.cuh) instead of a count.  The class-counted tail is off when
+// listing; add() is never reached and flags a consistency error if it is.
+struct ListSink {
+    static constexpr bool kList = true;
+    ListRing ring;
+    unsigned long long tail_seen;   // lane 0
+    int* err;
+    __device__ __forceinline__ void add(int, unsigned long long) { atomicCAS(err, 0, DEV_ECHECK + 9); }
 };
 
 // one leaf per active lane under pattern pid: one add per distinct pattern
@@ -522,6 +537,54 @@ __device__ __noinline__ void mt_tail_agg(const MotifWalk& a, MtWarp* W, int l, c
     __syncwarp();
 }
 
+// The leaves below the (l+1)-set tr + w (tr = W->sub[0 .. l-1]) as records
+// (tr, w, x; pattern id): first the exclusive neighbours x of w (adjacent to
+// w alone among the set: one pattern), marking every neighbour of w on the
+// way, then the remaining entries x of ext_l, whose adjacency to the set is
+// read from the marks.  The same leaves, in the same classes, as the
+// counting path above.
+template <class Sink>
+__device__ __forceinline__ void mt_list_leaves(const MotifWalk& a, MtWarp* W, int l, int c, const int32_t* ext,
+                                               int w, int wb, int we, int codew, Sink& sink,
+                                               unsigned long long& unit_leaves, int lane) {
+    const int offk = mt_code_off(l + 1);
+    const unsigned char low = (unsigned char)(0x80 | ((1u << l) - 1));
+    const int pid_x = a.lut[codew | ((1 << l) << offk)];
+    if (pid_x == 0xffff && lane == 0) atomicExch(a.err, DEV_EINVAL);
+    for (int t0 = wb; t0 < we; t0 += 32) {
+        const int t = t0 + lane;
+        bool act = false;
+        int x = 0;
+        if (t < we) {
+            x = a.indices[t];
+            const unsigned char m = a.mk[x - a.mbase];
+            act = (m & low) == 0;
+            a.mk[x - a.mbase] = m | (unsigned char)(1u << l);
+        }
+        unit_leaves += act ? 1u : 0u;
+        lr_emit(sink.ring, sink.tail_seen, W->sub, l, w, x, pid_x, act, lane);
+    }
+    __syncwarp();
+    const int len = W->len[l];
+    const unsigned lowk = (1u << (l + 1)) - 1u;
+    for (int j0 = c + 1; j0 < len; j0 += 32) {
+        const int j = j0 + lane;
+        const bool act = j < len;
+        int pid = 0, x = 0;
+        if (act) {
+            x = ext[j];
+            const int sig = a.mk[x - a.mbase] & lowk;
+            pid = a.lut[codew | (sig << offk)];
+            if (pid == 0xffff) atomicExch(a.err, DEV_EINVAL);
+            unit_leaves++;
+        }
+        lr_emit(sink.ring, sink.tail_seen, W->sub, l, w, x, pid, act, lane);
+    }
+    __syncwarp();
+    for (int t = wb + lane; t < we; t += 32) a.mk[a.indices[t] - a.mbase] &= (unsigned char)~(1u << l);
+    __syncwarp();
+}
+
 // Walk the unit whose node is at depth pdepth (W->cur/hi/len[pdepth] set,
 // unit_ext = its extension array).  Returns false if it stopped on a device
 // error (marks are then left dirty).  unit_leaves: lane-private leaf count.
@@ -564,41 +627,46 @@ __device__ __forceinline__ bool mt_walk(const MotifWalk& a, MtWarp* W, int pdept
         if (lane == 0 && l + 1 != k - 1) scanned += (unsigned)(we - wb);
         const unsigned char low = (unsigned char)(0x80 | ((1u << l) - 1));
         if (l + 1 == k - 1) {
-            // ---- last level: leaves of the (k-1)-set tr + w
-            const int offk = mt_code_off(l + 1);
-            if (lane == 0) scanned += 2ull * (unsigned)(we - wb);
-            int excl = 0;
-            for (int t = wb + lane; t < we; t += 32) {
-                const int x = a.indices[t];
-                const unsigned char m = a.mk[x - a.mbase];
-                excl += (m & low) == 0 ? 1 : 0;
-                a.mk[x - a.mbase] = m | (unsigned char)(1u << l);
-            }
-            excl = __reduce_add_sync(GPM_FULL_MASK, (unsigned)excl);
-            __syncwarp();
-            if (excl && lane == 0) {
-                const int pid = a.lut[codew | ((1 << l) << offk)];
-                if (pid == 0xffff) atomicExch(a.err, DEV_EINVAL);
-                else sink.add(pid, (unsigned long long)excl);
-                unit_leaves += (unsigned)excl;
-            }
-            const int len = W->len[l];
-            const unsigned lowk = (1u << (l + 1)) - 1u;
-            for (int j0 = c + 1; j0 < len; j0 += 32) {
-                const int j = j0 + lane;
-                const bool act = j < len;
-                int pid = 0;
-                if (act) {
-                    const int x = ext[j];
-                    const int sig = a.mk[x - a.mbase] & lowk;
-                    pid = a.lut[codew | (sig << offk)];
-                    unit_leaves++;
+            if constexpr (Sink::kList) {
+                // ---- last level, listing: a record per leaf of tr + w
+                mt_list_leaves(a, W, l, c, ext, w, wb, we, codew, sink, unit_leaves, lane);
+            } else {
+                // ---- last level: leaves of the (k-1)-set tr + w
+                const int offk = mt_code_off(l + 1);
+                if (lane == 0) scanned += 2ull * (unsigned)(we - wb);
+                int excl = 0;
+                for (int t = wb + lane; t < we; t += 32) {
+                    const int x = a.indices[t];
+                    const unsigned char m = a.mk[x - a.mbase];
+                    excl += (m & low) == 0 ? 1 : 0;
+                    a.mk[x - a.mbase] = m | (unsigned char)(1u << l);
                 }
-                mt_count_leaves(sink, act, pid, a.err);
+                excl = __reduce_add_sync(GPM_FULL_MASK, (unsigned)excl);
+                __syncwarp();
+                if (excl && lane == 0) {
+                    const int pid = a.lut[codew | ((1 << l) << offk)];
+                    if (pid == 0xffff) atomicExch(a.err, DEV_EINVAL);
+                    else sink.add(pid, (unsigned long long)excl);
+                    unit_leaves += (unsigned)excl;
+                }
+                const int len = W->len[l];
+                const unsigned lowk = (1u << (l + 1)) - 1u;
+                for (int j0 = c + 1; j0 < len; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool act = j < len;
+                    int pid = 0;
+                    if (act) {
+                        const int x = ext[j];
+                        const int sig = a.mk[x - a.mbase] & lowk;
+                        pid = a.lut[codew | (sig << offk)];
+                        unit_leaves++;
+                    }
+                    mt_count_leaves(sink, act, pid, a.err);
+                }
+                __syncwarp();
+                for (int t = wb + lane; t < we; t += 32) a.mk[a.indices[t] - a.mbase] &= (unsigned char)~(1u << l);
+                __syncwarp();
             }
-            __syncwarp();
-            for (int t = wb + lane; t < we; t += 32) a.mk[a.indices[t] - a.mbase] &= (unsigned char)~(1u << l);
-            __syncwarp();
         } else {
             // ---- push w: ext_{l+1} = ext_l[c+1:] ++ exclusive neighbours of w
             if (!mt_push(a, W, l, c, ext, w, wb, we, codew, lane)) return false;

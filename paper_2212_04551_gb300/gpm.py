@@ -69,6 +69,10 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 
+# int32 consumer(const int32* records, int64 count, int32 record_words, void* user)
+GPM_LIST_CONSUMER = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_void_p)
+
 # name -> (restype, argtypes); every symbol include/gpm.h declares
 SIGNATURES = {
     "gpm_graph_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]),
@@ -107,6 +111,8 @@ SIGNATURES = {
                                            ctypes.POINTER(gpm_monitor_stats)]),
     "gpm_selftest_sum": (ctypes.c_int, [_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _u64p]),
     "gpm_measure_l2": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "gpm_list": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, ctypes.c_int64, GPM_LIST_CONSUMER,
+                                ctypes.c_void_p, _u64p]),
 }
 GPM_MLP_PARAMS = 4801
 
@@ -267,6 +273,34 @@ def gpm_clique_count_dfs(g: Graph, k: int) -> int:
     """k-cliques by the paper's DM_DFS baseline (one thread per root)."""
     out = ctypes.c_uint64()
     _check(load().gpm_clique_count_dfs(g, int(k), ctypes.byref(out)), "gpm_clique_count_dfs")
+    return out.value
+
+
+def gpm_list(g: Graph, app: int, k: int, consumer, pattern: int = -1, ring_records: int = 0) -> int:
+    """List every k-clique (app CLIQUE) or connected induced k-subgraph (app
+    MOTIF; ``pattern`` >= 0 lists that pattern's only) through the host ring.
+
+    ``consumer(records)`` gets an int32 array of shape (count, k + 1) -- k
+    vertex ids, then the pattern id (motifs) or -1 (cliques) -- valid during
+    the call only (copy what you keep); returning True stops the listing.
+    Returns the number of records delivered.  An exception raised by the
+    consumer stops the listing and is raised again here."""
+    errors = []
+
+    def _cb(ptr, count, words, _user):
+        try:
+            arr = np.ctypeslib.as_array(ptr, shape=(int(count) * int(words),)).reshape(int(count), int(words))
+            return 1 if consumer(arr) else 0
+        except BaseException as e:  # noqa: BLE001 -- handed back to the caller below
+            errors.append(e)
+            return 1
+
+    cb = GPM_LIST_CONSUMER(_cb)
+    out = ctypes.c_uint64()
+    st = load().gpm_list(g, int(app), int(k), int(pattern), int(ring_records), cb, None, ctypes.byref(out))
+    if errors:
+        raise errors[0]
+    _check(st, "gpm_list")
     return out.value
 
 
