@@ -15,7 +15,11 @@ every root of an R-MAT scale-16 graph (plain vs learned scheduling, plus
 6- and 7-vertex motifs on a stratified root sample), 4,096 small
 Barabasi-Albert graphs (batched launch vs the plain kernel on their union
 vs one plain call per graph), and deep cliques plus 6-vertex motifs on a
-stochastic block model graph (plain vs learned).
+stochastic block model graph (plain vs learned).  Then the load-balancing
+and DM_DFS ablations and subgraph listing through the host ring
+(``listing``: records per second to a counting consumer).  ``--full`` adds
+the long comparisons (learned over every R-MAT root, DM_DFS at k = 5, no
+balancing on the 7-cliques), about five more minutes.
 
 Printed: one JSON line (rank 0) with the metric, the device-timed value,
 the end-to-end value through the C ABI with host buffers (graph creation
@@ -68,6 +72,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k8", action="store_true", help="skip the timed k = 4..8 enumeration")
     ap.add_argument("--no-configs", action="store_true", help="skip the per-workload entries")
+    ap.add_argument("--full", action="store_true",
+                    help="also the long comparisons: learned over every rmat16 root, DM_DFS at k = 5, "
+                         "no balancing on chunglu1m 7-cliques")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one small launch of a kernel (for ncu captures) and exit")
     return ap.parse_args()
@@ -414,7 +421,7 @@ def config_er516(stream) -> dict:
             "oracle_parity": (by_code(4, c) == want and by_code(4, bm[0]) == want) if want else None}
 
 
-def config_rmat16(stream, learned: Learned) -> dict:
+def config_rmat16(stream, learned: Learned, full: bool = False) -> dict:
     """5-vertex motifs over every root of R-MAT scale 16 (hub of degree 6,444
     at id 0), plain and learned; pinned by the star identity
     sum_p dom(p) count_p = sum_v C(d(v), 4).  6- and 7-vertex motifs on the
@@ -425,7 +432,7 @@ def config_rmat16(stream, learned: Learned) -> dict:
     dg = gpm.graph_from_csr(g, stream=stream)
     d = g.degrees()
     res = {"workload": "rmat16 motif k=5 every root (R-MAT scale 16, edge factor 8, seed 2)"}
-    cmp5, c5, _ = learned.compare(dg, g, 5, None, reps=1, arms=("plain", "learned"))
+    cmp5, c5, _ = learned.compare(dg, g, 5, None, reps=1, arms=("plain", "learned") if full else ("plain",))
     lhs = sum(dominating(5, gpm.gpm_motif_pattern(5, p)) * int(x) for p, x in enumerate(c5))
     res["k5_all_roots"] = {"subgraphs": int(c5.sum()), **cmp5,
                            "star_identity": lhs == sum(comb(int(x), 4) for x in d),
@@ -534,7 +541,7 @@ def config_sbm2000(stream, learned: Learned) -> dict:
     return res
 
 
-def balancing_ablation(stream) -> dict:
+def balancing_ablation(stream, full: bool = False) -> dict:
     """Load balancing on the same kernels and GB300 (the paper's Section
     4.3.5 and Table optimizations-performance, on this hardware): the
     in-kernel hand-off (the plain method's default), the paper's
@@ -561,19 +568,20 @@ def balancing_ablation(stream) -> dict:
         c, mst = gpm.gpm_count_monitored(dg, app, k, th)
         res["host_monitored"] = {"ms": (time.perf_counter() - t0) * 1000.0, "threshold": th, **mst,
                                  "same_counts": bool(np.array_equal(c, ref))}
-        gpm.gpm_set_config(dg, donate=0)
-        c = gpm.gpm_clique_count(dg, k) if app == gpm.GPM_APP_CLIQUE else gpm.gpm_motif_count(dg, k)
-        st = gpm.gpm_get_stats(dg)
-        res["none"] = {"kernel_ms": st["kernel_ms"], "idle_warp_frac": st["idle_warp_frac"],
-                       "same_counts": bool(np.array_equal(np.ravel(c), np.ravel(ref)))}
         res["speedup_handoff_vs_monitored"] = res["host_monitored"]["ms"] / res["in_kernel_handoff"]["ms"]
-        res["speedup_handoff_vs_none"] = res["none"]["kernel_ms"] / res["in_kernel_handoff"]["kernel_ms"]
+        if full or app != gpm.GPM_APP_CLIQUE:
+            gpm.gpm_set_config(dg, donate=0)
+            c = gpm.gpm_clique_count(dg, k) if app == gpm.GPM_APP_CLIQUE else gpm.gpm_motif_count(dg, k)
+            st = gpm.gpm_get_stats(dg)
+            res["none"] = {"kernel_ms": st["kernel_ms"], "idle_warp_frac": st["idle_warp_frac"],
+                           "same_counts": bool(np.array_equal(np.ravel(c), np.ravel(ref)))}
+            res["speedup_handoff_vs_none"] = res["none"]["kernel_ms"] / res["in_kernel_handoff"]["kernel_ms"]
         out[f"{name}_{'clique' if app == gpm.GPM_APP_CLIQUE else 'motif'}{k}"] = res
         dg.close()
     return out
 
 
-def dm_dfs_ablation(stream) -> dict:
+def dm_dfs_ablation(stream, full: bool = False) -> dict:
     """The paper's DM_DFS baseline (one thread per root, sorted-list merges,
     no balancing) against the warp-centric bitmap kernel with hand-offs, on
     chunglu1m cliques k = 4 and 5 (the paper's Table optimizations-
@@ -583,7 +591,7 @@ def dm_dfs_ablation(stream) -> dict:
     g = G.workload("chunglu1m")
     dg = gpm.graph_from_csr(g, stream=stream)
     out = {}
-    for k in (4, 5):
+    for k in ((4, 5) if full else (4,)):
         c = gpm.gpm_clique_count(dg, k)
         wc = gpm.gpm_get_stats(dg)["kernel_ms"]
         cd = gpm.gpm_clique_count_dfs(dg, k)
@@ -591,6 +599,48 @@ def dm_dfs_ablation(stream) -> dict:
         out[f"k{k}"] = {"dm_dfs_kernel_ms": dfs, "warp_bitmap_kernel_ms": wc, "speedup": dfs / wc,
                         "same_counts": cd == c, "cliques": c}
     dg.close()
+    return out
+
+
+def listing_entry(stream) -> dict:
+    """Subgraph listing (aggregate_store) through gpm_list: records per
+    second delivered to a host consumer that counts them (motifs: by
+    pattern, checked against gpm_motif_count), wall time of the whole call
+    (the kernel writes into mapped host memory, the calling thread consumes
+    while it runs)."""
+    import torch
+    from paper_2212_04551_gb300 import gpm
+    from paper_2212_04551_gb300 import graphs as G
+    out = {}
+    for name, app, k in (("rmat16", gpm.GPM_APP_CLIQUE, 4), ("rmat16", gpm.GPM_APP_CLIQUE, 5),
+                         ("sbm2000", gpm.GPM_APP_CLIQUE, 6), ("er516", gpm.GPM_APP_MOTIF, 4),
+                         ("sbm2000", gpm.GPM_APP_MOTIF, 4)):
+        g = G.workload(name)
+        dg = gpm.graph_from_csr(g, stream=stream)
+        if app == gpm.GPM_APP_CLIQUE:
+            want = np.array([gpm.gpm_clique_count(dg, k)], dtype=np.uint64)
+        else:
+            want = gpm.gpm_motif_count(dg, k)
+        tally = np.zeros(want.shape[0], dtype=np.int64)
+
+        def consume(recs):
+            if app == gpm.GPM_APP_CLIQUE:
+                tally[0] += recs.shape[0]
+            else:
+                tally[:] += np.bincount(recs[:, k], minlength=tally.shape[0])
+            return False
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = gpm.gpm_list(dg, app, k, consume, ring_records=1 << 20)
+        wall = time.perf_counter() - t0
+        kern = gpm.gpm_get_stats(dg)["kernel_ms"]
+        what = "clique" if app == gpm.GPM_APP_CLIQUE else "motif"
+        out[f"{name}_{what}{k}"] = {"records": int(n), "wall_ms": wall * 1000.0, "kernel_ms": kern,
+                                   "records_per_s": n / wall if wall > 0 else None,
+                                   "ring_records": 1 << 20, "record_bytes": 4 * (k + 2),
+                                   "same_as_counts": bool(np.array_equal(tally.astype(np.uint64), want))}
+        dg.close()
     return out
 
 
@@ -831,9 +881,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_configs:
         learned = Learned(stream)
         line["learned_training"] = learned.info
-        line["configs"] = {"er516": config_er516(stream), "rmat16": config_rmat16(stream, learned),
+        line["configs"] = {"er516": config_er516(stream), "rmat16": config_rmat16(stream, learned, args.full),
                            "ba4096": config_ba4096(stream), "sbm2000": config_sbm2000(stream, learned)}
-        line["ablations"] = {"balancing": balancing_ablation(stream), "dm_dfs": dm_dfs_ablation(stream)}
+        line["ablations"] = {"balancing": balancing_ablation(stream, args.full),
+                             "dm_dfs": dm_dfs_ablation(stream, args.full)}
+        line["listing"] = listing_entry(stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, cores, _, _ = cpu_baseline(g, args.k_lo, args.k_hi, args.cpu_stride)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

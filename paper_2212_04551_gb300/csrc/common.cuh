@@ -228,6 +228,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
 struct ListRing;
 ListRing list_ring_of(const ListJob* job, Control* ctl);
 void list_drain(ListJob* job, gpm_graph* g, Control* ctl);
+std::string list_where(const ListJob* job);
 void launch_clique_store(gpm_graph* g, int k, const ListRing& ring, Control* ctl);
 void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_records, gpm_list_consumer consumer,
               void* user, uint64_t* delivered);

@@ -35,6 +35,7 @@ struct ListJob {
     void* user = nullptr;
     uint64_t delivered = 0;
     bool stopped = false;
+    std::string where;                     // the ring's state when a listing ended early
     cudaStream_t stream = nullptr;         // the launch's stream
     bool launched = false;
 
@@ -59,6 +60,8 @@ ListRing list_ring_of(const ListJob* j, Control* ctl) {
     r.tag_filter = j->tag_filter;
     return r;
 }
+
+std::string list_where(const ListJob* j) { return j->where; }
 
 // Take the records of the launch that ends at g->ev1, in order, until it has
 // ended and everything it reserved is taken (or the listing stopped / failed).
@@ -112,7 +115,13 @@ void list_drain(ListJob* j, gpm_graph* g, Control* ctl) {
             GPM_CUDA(cudaMemcpyAsync(&head_end, j->head.ptr, sizeof(head_end), cudaMemcpyDeviceToHost, side));
             GPM_CUDA(cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, side));
             GPM_CUDA(cudaStreamSynchronize(side));
-            if (j->stopped || err) break;   // an aborted launch leaves reserved records unwritten
+            if (j->stopped || err) {         // an aborted launch leaves reserved records unwritten
+                const int32_t* rec = j->host_rec + (size_t)(tail % j->cap) * j->stride;
+                j->where = "host took " + std::to_string(tail) + " of " + std::to_string(head_end) +
+                           " reserved records; the next slot holds sequence " +
+                           std::to_string(__atomic_load_n(reinterpret_cast<const uint32_t*>(rec), __ATOMIC_ACQUIRE));
+                break;
+            }
             ended = true;                   // everything reserved is written: take the rest
             continue;
         }
@@ -185,8 +194,7 @@ void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_record
         GPM_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
         g->stats.kernel_ms = ms;
         if (h.error == DEV_ETIMEOUT)
-            fail(GPM_ETIMEOUT, "the ring stayed full for longer than max_idle_ms (" + std::to_string(j.delivered) +
-                                   " records delivered)");
+            fail(GPM_ETIMEOUT, "the ring stayed full for longer than max_idle_ms (" + j.where + ")");
         if (h.error && h.error != DEV_STOPPED) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
     }
 }

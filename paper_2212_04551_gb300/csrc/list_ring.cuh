@@ -34,13 +34,25 @@ struct ListRing {
     int tag_filter;                             // >= 0: only records with this tag
 };
 
+// The host's count of consumed records (system-scope acquire: the host
+// thread writes it) and the release of a record's sequence word (after the
+// record, at system scope: the host thread reads it).
+__device__ __forceinline__ unsigned long long lr_load_tail(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void lr_publish(int32_t* p, int32_t v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Lane 0: reserve n records; their first position, or ~0 when the listing
 // is over (stop, error, or no host progress for max_wait_ns).
 __device__ __forceinline__ unsigned long long lr_reserve(const ListRing& r, int n, unsigned long long& tail_seen) {
     if (*(volatile int*)&r.ctl->error) return ~0ull;
     const unsigned long long pos = atomicAdd(r.head, (unsigned long long)n);
     if (pos + n <= tail_seen + r.cap) return pos;
-    unsigned long long t = *(const volatile unsigned long long*)r.tail;
+    unsigned long long t = lr_load_tail(r.tail);
     unsigned long long last = t, since = gpm_globaltimer();
     while (pos + n > t + r.cap) {
         if (*(volatile int*)&r.ctl->error) return ~0ull;
@@ -53,7 +65,7 @@ __device__ __forceinline__ unsigned long long lr_reserve(const ListRing& r, int 
             return ~0ull;
         }
         __nanosleep(512);
-        t = *(const volatile unsigned long long*)r.tail;
+        t = lr_load_tail(r.tail);
     }
     tail_seen = t;
     return pos;
@@ -79,8 +91,7 @@ __device__ __forceinline__ bool lr_emit(const ListRing& r, unsigned long long& t
         if (mid >= 0) rec[o++] = mid;
         rec[o++] = x;
         rec[o] = tag;
-        __threadfence_system();   // the record before its sequence word
-        *(volatile int32_t*)rec = (int32_t)(uint32_t)(q + 1);
+        lr_publish(rec, (int32_t)(uint32_t)(q + 1));
     }
     return true;
 }

@@ -227,6 +227,8 @@ def test_slow_consumer_times_out_and_recovers():
     assert e.value.status == gpm.GPM_ETIMEOUT
     gpm.gpm_set_config(dg, max_idle_ms=120000)
     col = Collect()
+    assert gpm.gpm_list(gpm.graph_from_csr(g), gpm.GPM_APP_CLIQUE, 4, col, ring_records=64) == total
+    col = Collect()
     assert gpm.gpm_list(dg, gpm.GPM_APP_CLIQUE, 4, col, ring_records=64) == total
     assert gpm.gpm_clique_count(dg, 4) == total
     m = gpm.gpm_motif_count(dg, 4)
