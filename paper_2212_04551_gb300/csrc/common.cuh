@@ -152,6 +152,7 @@ struct alignas(128) Control {
     alignas(128) unsigned long long heavy_next;   // clique list path: next (heavy root, chunk) unit
     int n_heavy;                                  // clique list path: roots above the bitmap limit
     int pad_heavy;
+    unsigned long long list_diag[3];              // listing: the first wait that ran out (position, count, tail seen)
 };
 
 // Device-side status values (mirrors gpm_status).
@@ -228,7 +229,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
 struct ListRing;
 ListRing list_ring_of(const ListJob* job, Control* ctl);
 void list_drain(ListJob* job, gpm_graph* g, Control* ctl);
-std::string list_where(const ListJob* job);
+std::string list_where(const ListJob* job, const Control& h);
 void launch_clique_store(gpm_graph* g, int k, const ListRing& ring, Control* ctl);
 void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_records, gpm_list_consumer consumer,
               void* user, uint64_t* delivered);

@@ -26,9 +26,9 @@ struct ListJob {
     unsigned long long cap = 0;            // records
     int32_t* host_rec = nullptr;           // mapped pinned ring
     int32_t* dev_rec = nullptr;
-    unsigned long long* host_tail = nullptr;   // mapped pinned: records consumed
-    unsigned long long* dev_tail = nullptr;
-    DevBuf head;                           // device: records reserved
+    unsigned long long* host_tail = nullptr;   // pinned: the count the next copy sends
+    unsigned long long* dev_tail = nullptr;    // device: records consumed (host copies)
+    DevBuf head;                           // device: records reserved, records consumed
     int tag_filter = -1;
     unsigned long long max_wait_ns = 0;
     gpm_list_consumer consumer = nullptr;
@@ -61,7 +61,14 @@ ListRing list_ring_of(const ListJob* j, Control* ctl) {
     return r;
 }
 
-std::string list_where(const ListJob* j) { return j->where; }
+std::string list_where(const ListJob* j, const Control& h) {
+    std::string s = j->where;
+    if (h.error == DEV_ETIMEOUT && h.list_diag[1])
+        s += "; the wait that ran out: records " + std::to_string(h.list_diag[0]) + " .. " +
+             std::to_string(h.list_diag[0] + h.list_diag[1] - 1) + " with " + std::to_string(h.list_diag[2]) +
+             " seen consumed";
+    return s;
+}
 
 // Take the records of the launch that ends at g->ev1, in order, until it has
 // ended and everything it reserved is taken (or the listing stopped / failed).
@@ -94,7 +101,12 @@ void list_drain(ListJob* j, gpm_graph* g, Control* ctl) {
         if (n) {
             idle_polls = 0;
             tail += n;
-            __atomic_store_n(j->host_tail, tail, __ATOMIC_RELEASE);   // the slots are free again
+            // the slots are free again: tell the device (a copy on the side
+            // stream runs beside the kernel)
+            *j->host_tail = tail;
+            GPM_CUDA(cudaMemcpyAsync(j->dev_tail, j->host_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                                     side));
+            GPM_CUDA(cudaStreamSynchronize(side));
             j->delivered += n;
             if (j->consumer(staging.data(), (int64_t)n, (int32_t)words, j->user) != 0 && !j->stopped) {
                 j->stopped = true;
@@ -165,17 +177,17 @@ void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_record
     j.user = user;
     const size_t ring_bytes = sizeof(int32_t) * (size_t)j.cap * j.stride;
     if (cudaHostAlloc(reinterpret_cast<void**>(&j.host_rec), ring_bytes, cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void**>(&j.host_tail), 64, cudaHostAllocMapped) != cudaSuccess) {
+        cudaHostAlloc(reinterpret_cast<void**>(&j.host_tail), 64, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         fail(GPM_ENOMEM, "mapped host ring of " + std::to_string(ring_bytes) + " bytes");
     }
     std::memset(j.host_rec, 0, ring_bytes);
     std::memset(j.host_tail, 0, 64);
     GPM_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&j.dev_rec), j.host_rec, 0));
-    GPM_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&j.dev_tail), j.host_tail, 0));
-    j.head.ensure(sizeof(unsigned long long));
+    j.head.ensure(2 * sizeof(unsigned long long));
+    j.dev_tail = j.head.as<unsigned long long>() + 1;
     cudaStream_t s = g->stream;
-    GPM_CUDA(cudaMemsetAsync(j.head.ptr, 0, sizeof(unsigned long long), s));
+    GPM_CUDA(cudaMemsetAsync(j.head.ptr, 0, 2 * sizeof(unsigned long long), s));
     j.launched = true;
 
     if (app == GPM_APP_MOTIF) {
@@ -194,7 +206,7 @@ void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_record
         GPM_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
         g->stats.kernel_ms = ms;
         if (h.error == DEV_ETIMEOUT)
-            fail(GPM_ETIMEOUT, "the ring stayed full for longer than max_idle_ms (" + j.where + ")");
+            fail(GPM_ETIMEOUT, "the ring stayed full for longer than max_idle_ms (" + list_where(&j, h) + ")");
         if (h.error && h.error != DEV_STOPPED) fail(GPM_ECUDA, "device error " + std::to_string(h.error));
     }
 }

@@ -7,9 +7,10 @@
 // words: a sequence word, the k vertex ids, and a tag (the pattern id of a
 // motif, -1 for a clique).  A warp reserves up to 32 consecutive records on
 // a device counter, waits (bounded) until the host has consumed far enough
-// for them to be free, writes them, fences, and then stores q + 1 in each
-// record's sequence word: the host takes records in order once their
-// sequence word matches, and publishes how many it has taken.  The record a
+// for them to be free, writes them, and then stores q + 1 in each record's
+// sequence word (a system-scope release): the host takes records in order
+// once their sequence word matches, and copies the count it has taken into
+// a device word.  The record a
 // host waits for is never behind a wait of its own writer (a reservation of
 // n <= 32 <= cap records at the host's position always fits), so the two
 // sides cannot block each other.  A stop (the consumer asked for it), an
@@ -28,18 +29,19 @@ struct ListRing {
     unsigned long long cap;                     // records (>= 32)
     int stride;                                 // words per record: 1 + k + 1
     unsigned long long* head;                   // device: records reserved
-    const unsigned long long* tail;             // mapped host: records consumed
+    const unsigned long long* tail;             // device: records consumed (written by the host's copies)
     Control* ctl;
     unsigned long long max_wait_ns;             // a wait without host progress longer than this fails
     int tag_filter;                             // >= 0: only records with this tag
 };
 
-// The host's count of consumed records (system-scope acquire: the host
-// thread writes it) and the release of a record's sequence word (after the
-// record, at system scope: the host thread reads it).
+// The host's count of consumed records: a device word that the host's copy
+// engine overwrites while the kernel runs (acquire: the slots it frees are
+// written after it is read).  The release of a record's sequence word: after
+// the record, at system scope (the host thread reads it from host memory).
 __device__ __forceinline__ unsigned long long lr_load_tail(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void lr_publish(int32_t* p, int32_t v) {
@@ -61,7 +63,11 @@ __device__ __forceinline__ unsigned long long lr_reserve(const ListRing& r, int 
             last = t;
             since = now;
         } else if (now - since > r.max_wait_ns) {
-            atomicCAS(&r.ctl->error, 0, DEV_ETIMEOUT);
+            if (atomicCAS(&r.ctl->error, 0, DEV_ETIMEOUT) == 0) {
+                r.ctl->list_diag[0] = pos;
+                r.ctl->list_diag[1] = (unsigned long long)n;
+                r.ctl->list_diag[2] = t;
+            }
             return ~0ull;
         }
         __nanosleep(512);

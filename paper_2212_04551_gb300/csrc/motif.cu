@@ -554,7 +554,7 @@ void run_motif(gpm_graph* g, int k, const int32_t* d_roots, int64_t n_roots,
     if (list && h.error == DEV_STOPPED) return;   // the consumer asked to stop
     if (list && h.error == DEV_ETIMEOUT)
         fail(GPM_ETIMEOUT, "the listing ring stayed full (or an idle warp waited) for longer than max_idle_ms (" +
-                               list_where(list) + ")");
+                               list_where(list, h) + ")");
     if (h.error == DEV_ETIMEOUT) fail(GPM_ETIMEOUT, "an idle warp waited longer than max_idle_ms without progress");
     if (h.error == DEV_EINVAL) fail(GPM_ECUDA, "pattern table lookup hit an invalid traversal code");
     if (h.error >= DEV_ECHECK) fail(GPM_ECUDA, "device consistency check " + std::to_string(h.error - DEV_ECHECK) + " failed");
