@@ -184,6 +184,12 @@ typedef struct {
     int32_t batch_split;       /* batched launch: roots heavier than 1/4096 of the total estimated   */
                                /* work are cut into this many units over ranges of their children    */
                                /* before the launch (0 or 1: none; at most 64)                       */
+    int32_t clique_cpl;        /* three-level clique tail (k >= 7): the k-cliques below each child of */
+                               /* a tail node are counted as the triangles of its candidate graph,    */
+                               /* sum_t C(a_t, 2) minus the open wedges found from the non-edges,     */
+                               /* instead of one AND + POPC per (k-1)-clique: 0 never, 1 always,      */
+                               /* 2..100 for tail nodes whose members are at least this percent       */
+                               /* pairwise adjacent (default 85)                                      */
 } gpm_config;
 
 #define GPM_ORDER_ID          0  /* roots in id order                               */
@@ -269,7 +275,12 @@ gpm_status gpm_clique_count_dfs(gpm_graph* g, int k, uint64_t* out_count);
  * gpm_motif_count count), in no particular order.  Kernel time is in
  * gpm_get_stats.  If the ring stays full for longer than max_idle_ms
  * (the consumer does not keep up), the device gives up: GPM_ETIMEOUT, with
- * the records delivered so far.
+ * the records delivered so far.  The consumer runs while the kernel runs
+ * and the kernel waits for it, so the consumer must not wait for the
+ * device: a call that synchronises with it (cudaFree, cudaDeviceSynchronize,
+ * a synchronous copy, gpm_graph_destroy, a count on the same stream) blocks
+ * until the listing kernel ends, which happens only when its wait for ring
+ * space runs out (GPM_ETIMEOUT after max_idle_ms).
  * Errors: GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT.
  */
 typedef int32_t (*gpm_list_consumer)(const int32_t* records, int64_t count, int32_t record_words, void* user);

@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams p) {
     cw.tail_levels = 0;
     cw.compact = 0;
     cw.compact3 = 0;
+    cw.cpl = 0;
     cw.monitor = false;
     cw.spill = nullptr;
     cw.spill_cap = 0;

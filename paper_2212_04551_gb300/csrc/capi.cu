@@ -372,6 +372,7 @@ gpm_status gpm_set_config(gpm_graph* g, const gpm_config* cfg) {
         if (c.motif_agg_min < 0) fail(GPM_EINVAL, "motif_agg_min < 0");
         if (c.clique_compact3 < 0 || c.clique_compact3 > 2) fail(GPM_EINVAL, "clique_compact3 must be 0, 1 or 2");
         if (c.batch_split < 0 || c.batch_split > 64) fail(GPM_EINVAL, "batch_split must be in [0, 64]");
+        if (c.clique_cpl < 0 || c.clique_cpl > 100) fail(GPM_EINVAL, "clique_cpl must be in [0, 100]");
         g->cfg = c;
     });
 }

@@ -69,6 +69,7 @@ struct CliqueParams {
     int tail_levels;
     int compact;
     int compact3;
+    int cpl;                    // three-level tail: deepest level through non-edges (policy of gpm_config)
     int monitor;                // host-monitored balancing (no donation): count active warps, obey stop
     CliqueUnit* spill;
     unsigned long long spill_cap;
@@ -117,6 +118,7 @@ __global__ void __maxnreg__(96) k_clique(CliqueParams p) {
     walk.tail_levels = p.tail_levels;
     walk.compact = p.compact;
     walk.compact3 = p.compact3;
+    walk.cpl = p.cpl;
     walk.monitor = p.monitor != 0;
     walk.spill = p.spill;
     walk.spill_cap = p.spill_cap;
@@ -370,6 +372,7 @@ static CliqueLaunch plan_clique_launch(gpm_graph* g, int k_lo, int k_hi, const i
     p.donate_min = std::max(2, g->cfg.donate_min);
     p.donate_after_ns = (unsigned long long)std::max(0, g->cfg.donate_after_us) * 1000ull;
     p.tail_levels = g->cfg.clique_tail;
+    p.cpl = g->cfg.clique_cpl;
     p.max_idle_ns = (unsigned long long)std::max(1, g->cfg.max_idle_ms) * 1000000ull;
     return c;
 }

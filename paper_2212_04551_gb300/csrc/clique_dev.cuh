@@ -224,6 +224,9 @@ struct CliqueWalk {
     int compact;                          // compacted two-level tail: 0 never, 1 large nodes, 2 whenever shorter
     int compact3;                         // compacted three-level tail whenever it shortens the rows (2: and
                                           // warp-cooperative pairs for nodes of at most 64 members)
+    int cpl;                              // three-level tail: count the deepest level through the
+                                          // non-edges (0 never, 1 always, 2..100 nodes at least this
+                                          // percent dense)
     // host-monitored balancing (the paper's stop / redistribute / restart):
     // when the host raises ctl->stop, the walk writes its remaining work as
     // units to spill[] and unwinds
@@ -453,6 +456,110 @@ __device__ __forceinline__ void cq_pairs_run(const uint32_t (&c)[W], const TriRo
     }
 }
 
+// The deepest level of the three-level tail counted through non-edges.  For
+// a child m of the tail node, X = its candidates (the vertices that extend
+// it); the k-cliques below m are the triangles of G[X].  With a_t = the
+// neighbours of t above t inside X, the sum over t of C(a_t, 2) counts every
+// triangle once (at its lowest vertex) plus every wedge u - t - v (t below
+// u < v) whose ends are not adjacent; those wedges are counted from the
+// non-edge side: for each non-adjacent pair u < v in X, the members t of X
+// below u adjacent to both.  So
+//     triangles(G[X]) = sum_t C(a_t, 2) - sum_{u<v in X, u !~ v} |{t < u : t ~ u, t ~ v}|,
+// and on a nearly complete G[X] the second sum has few terms: the work per
+// pair (m, t) is one AND + POPC instead of one per (k-1)-clique through it.
+// A pair (m, j) adds C(a_j, 2) to P and its non-edges' wedge counts to Q; a
+// node's P - Q is exact once all its pairs are in (the caller sums the warp).
+__device__ __forceinline__ uint32_t bits_above(int b) { return b >= 31 ? 0u : (0xffffffffu << (b + 1)); }
+__device__ __forceinline__ uint32_t bits_below(int b) { return (1u << b) - 1u; }
+
+// x: X (the candidates of the pair's first member), j: the pair's second
+// member, rows: upper rows (row(t)[z] valid for z >= t / 32).  Returns a_j
+// (the (k-1)-cliques through the pair).
+template <int W, class Rows>
+__device__ __forceinline__ int cq_cpl_pair(const uint32_t (&x)[W], const Rows& rows, int w, int j,
+                                           unsigned long long& P, unsigned long long& Q,
+                                           unsigned long long& wops) {
+    const uint32_t* rj = rows.row(j);
+    const int bj = j >> 5;
+    uint32_t u[W];
+    int a = 0;
+    bool any = false;
+#pragma unroll
+    for (int z = 0; z < W; z++) {
+        uint32_t r = 0u;
+        if (z >= bj && z < w) r = rj[z];
+        a += __popc(x[z] & r);
+        uint32_t nb = x[z] & ~r;                 // members of X not adjacent to j ...
+        nb &= z < bj ? 0u : (z == bj ? bits_above(j & 31) : 0xffffffffu);   // ... above j
+        u[z] = nb;
+        any |= nb != 0u;
+    }
+    P += (unsigned long long)(a * (a - 1) / 2);
+    wops += (unsigned)w;
+    if (any) {
+#pragma unroll
+        for (int zv = 0; zv < W; zv++) {
+            uint32_t nb = u[zv];
+            while (nb) {
+                const int v = 32 * zv + __ffs(nb) - 1;
+                nb &= nb - 1u;
+                // members t of X below j adjacent to j and to v
+                unsigned q = 0;
+#pragma unroll
+                for (int zt = 0; zt < W; zt++) {
+                    if (zt > bj) break;
+                    uint32_t tb = x[zt] & (zt < bj ? 0xffffffffu : bits_below(j & 31));
+                    while (tb) {
+                        const int t = 32 * zt + __ffs(tb) - 1;
+                        tb &= tb - 1u;
+                        const uint32_t* rt = rows.row(t);
+                        q += (rt[bj] >> (j & 31)) & (rt[v >> 5] >> (v & 31)) & 1u;
+                        wops += 1;
+                    }
+                }
+                Q += q;
+            }
+        }
+    }
+    return a;
+}
+
+// sum P, Q over the warp and add P - Q (>= 0 for whole nodes) to lane 0's kk
+__device__ __forceinline__ void cq_cpl_fold(unsigned long long P, unsigned long long Q, unsigned long long& kk,
+                                            int lane) {
+    for (int o = 16; o > 0; o >>= 1) {
+        P += __shfl_xor_sync(GPM_FULL_MASK, P, o);
+        Q += __shfl_xor_sync(GPM_FULL_MASK, Q, o);
+    }
+    if (lane == 0) kk += P - Q;
+}
+
+// whether a node of c members with e edges among them takes the non-edge
+// count (policy as CliqueWalk::cpl)
+__device__ __forceinline__ bool cq_cpl_dense(int policy, long long e, int c) {
+    if (policy <= 0 || c < 3) return false;
+    if (policy == 1) return true;
+    return 200ll * e >= (long long)policy * c * (c - 1);
+}
+
+// cq_pairs_run with the deepest level counted through non-edges
+template <int W>
+__device__ __forceinline__ void cq_pairs_run_cpl(const uint32_t (&c)[W], const TriRows& rows, int w,
+                                                 const int* pairs, int np, unsigned long long& km1,
+                                                 unsigned long long& P, unsigned long long& Q,
+                                                 unsigned long long& wops, int lane) {
+    for (int t = lane; t < np; t += 32) {
+        const int pr = pairs[t];
+        const int pi = pr >> 16;
+        const int bi = pi >> 5;
+        const uint32_t* ri = rows.row(pi);
+        uint32_t x[W];
+#pragma unroll
+        for (int z = 0; z < W; z++) x[z] = (z >= bi && z < w) ? (c[z] & ri[z]) : 0u;
+        km1 += (unsigned)cq_cpl_pair<W>(x, rows, w, pr & 0xffff, P, Q, wops);
+    }
+}
+
 // The last three levels below a node of size k-4 with candidates C and
 // children in [from, to): its children i are walked in order (warp-uniform);
 // the grandchildren j of each (bits of C & row_i) are appended to a shared
@@ -464,10 +571,27 @@ template <int W>
 __device__ __forceinline__ void cq_tail3(const uint32_t* C, const TriRows& rows, int w, int from, int to,
                                          int* pairs, unsigned long long& n3, unsigned long long& n2,
                                          unsigned long long& km1, unsigned long long& kk, unsigned long long& wops,
-                                         int lane) {
+                                         int lane, int cpl) {
     uint32_t c[W];
 #pragma unroll
     for (int z = 0; z < W; z++) c[z] = z < w ? C[z] : 0u;
+    bool dense = false;
+    if (cpl > 0) {
+        // edges among the node's members (one row AND per member)
+        int cnt = 0, e = 0;
+        for (int q = 0; q < w; q++) {
+            const uint32_t word = c[q];
+            cnt += __popc(word);
+            if ((word >> lane) & 1u) {
+                const int p = 32 * q + lane;
+                const uint32_t* rp = rows.row(p);
+                for (int z = q; z < w; z++) e += __popc(C[z] & rp[z]);
+            }
+        }
+        e = (int)__reduce_add_sync(GPM_FULL_MASK, (unsigned)e);
+        dense = cq_cpl_dense(cpl, e, cnt);
+    }
+    unsigned long long P = 0, Q = 0;
     int np = 0;
     for (int q = 0; q < w; q++) {
         uint32_t word = C[q] & range_mask(q, from, to);
@@ -487,7 +611,10 @@ __device__ __forceinline__ void cq_tail3(const uint32_t* C, const TriRows& rows,
             if (np >= CQ_PAIR_FLUSH) {
                 __syncwarp();
                 n2 += (unsigned)np;
-                cq_pairs_run<W>(c, rows, w, pairs, np, km1, kk, wops, lane);
+                if (dense)
+                    cq_pairs_run_cpl<W>(c, rows, w, pairs, np, km1, P, Q, wops, lane);
+                else
+                    cq_pairs_run<W>(c, rows, w, pairs, np, km1, kk, wops, lane);
                 __syncwarp();
                 np = 0;
             }
@@ -496,21 +623,25 @@ __device__ __forceinline__ void cq_tail3(const uint32_t* C, const TriRows& rows,
     if (np) {
         __syncwarp();
         n2 += (unsigned)np;
-        cq_pairs_run<W>(c, rows, w, pairs, np, km1, kk, wops, lane);
+        if (dense)
+            cq_pairs_run_cpl<W>(c, rows, w, pairs, np, km1, P, Q, wops, lane);
+        else
+            cq_pairs_run<W>(c, rows, w, pairs, np, km1, kk, wops, lane);
         __syncwarp();
     }
+    if (dense) cq_cpl_fold(P, Q, kk, lane);
 }
 
 __device__ __forceinline__ void cq_tail3_dispatch(const uint32_t* C, const TriRows& rows, int w, int from, int to,
                                                   int* pairs, unsigned long long& n3, unsigned long long& n2,
                                                   unsigned long long& km1, unsigned long long& kk,
-                                                  unsigned long long& wops, int lane) {
-    if (w <= 1) cq_tail3<1>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 2) cq_tail3<2>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 4) cq_tail3<4>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 6) cq_tail3<6>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else if (w <= 8) cq_tail3<8>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
-    else cq_tail3<10>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane);
+                                                  unsigned long long& wops, int lane, int cpl) {
+    if (w <= 1) cq_tail3<1>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
+    else if (w <= 2) cq_tail3<2>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
+    else if (w <= 4) cq_tail3<4>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
+    else if (w <= 6) cq_tail3<6>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
+    else if (w <= 8) cq_tail3<8>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
+    else cq_tail3<10>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
 }
 
 // The last three levels below a node of size k-4, on the node's own members
@@ -544,10 +675,25 @@ __device__ __forceinline__ void cq_pairs_run_c(const uint32_t* R, int ws2, int w
 }
 
 template <int W2>
+__device__ __forceinline__ void cq_pairs_run_c_cpl(const uint32_t* R, int ws2, int w2, const int* pairs, int np,
+                                                   unsigned long long& km1, unsigned long long& P,
+                                                   unsigned long long& Q, unsigned long long& wops, int lane) {
+    const RectRows rr{R, ws2};
+    for (int t = lane; t < np; t += 32) {
+        const int pr = pairs[t];
+        const uint32_t* r1 = R + (pr >> 16) * ws2;
+        uint32_t x[W2];
+#pragma unroll
+        for (int z = 0; z < W2; z++) x[z] = z < w2 ? r1[z] : 0u;
+        km1 += (unsigned)cq_cpl_pair<W2>(x, rr, w2, pr & 0xffff, P, Q, wops);
+    }
+}
+
+template <int W2>
 __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows, int w, int c, int from, int to,
                                           int* mem, uint32_t* R, unsigned long long& n3, unsigned long long& n2,
                                           unsigned long long& km1, unsigned long long& kk,
-                                          unsigned long long& wops, int lane, bool coop) {
+                                          unsigned long long& wops, int lane, bool coop, int cpl) {
     int n = 0, m_lo = 0, m_hi = 0;
     for (int q = 0; q < w; q++) {
         const uint32_t word = C[q];
@@ -565,6 +711,7 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
     int pm[W2];
 #pragma unroll
     for (int b = 0; b < W2; b++) pm[b] = (b < w2 && 32 * b + lane < c) ? mem[32 * b + lane] : -1;
+    long long edges = 0;                  // among the members (warp-uniform)
     for (int m = 0; m < c; m++) {
         const int pmm = mem[m];
         const uint32_t* row = rows.row(pmm);
@@ -577,6 +724,7 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
                     const bool bit = pm[b] > pmm && ((row[pm[b] >> 5] >> (pm[b] & 31)) & 1u);
                     word = __ballot_sync(GPM_FULL_MASK, bit);
                 }
+                edges += __popc(word);
                 if (lane == b) Rm[b] = word;
             }
         }
@@ -584,7 +732,8 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
     __syncwarp();
     if (lane == 0) wops += (unsigned long long)c * (unsigned)w2;
     n3 += (unsigned)(m_hi - m_lo);
-    if (W2 <= 2 && coop) {
+    const bool dense = cq_cpl_dense(cpl, edges, c);
+    if (W2 <= 2 && coop && !dense) {
         // at most 64 members: the warp takes the pairs one at a time, lane t
         // holding the rows of members t and t + 32, and for a pair with
         // candidates y adds popc(y & R[t]) when t is in y -- every lane works
@@ -621,6 +770,7 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
         __syncwarp();
         return;
     }
+    unsigned long long P = 0, Q = 0;
     int np = 0;
     for (int m1 = m_lo; m1 < m_hi; m1++) {
         const uint32_t* r1 = R + m1 * ws2;
@@ -634,7 +784,10 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
         if (np >= CQ_PAIR_FLUSH) {
             __syncwarp();
             n2 += (unsigned)np;
-            cq_pairs_run_c<W2>(R, ws2, w2, pairs, np, km1, kk, wops, lane);
+            if (dense)
+                cq_pairs_run_c_cpl<W2>(R, ws2, w2, pairs, np, km1, P, Q, wops, lane);
+            else
+                cq_pairs_run_c<W2>(R, ws2, w2, pairs, np, km1, kk, wops, lane);
             __syncwarp();
             np = 0;
         }
@@ -642,8 +795,12 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
     if (np) {
         __syncwarp();
         n2 += (unsigned)np;
-        cq_pairs_run_c<W2>(R, ws2, w2, pairs, np, km1, kk, wops, lane);
+        if (dense)
+            cq_pairs_run_c_cpl<W2>(R, ws2, w2, pairs, np, km1, P, Q, wops, lane);
+        else
+            cq_pairs_run_c<W2>(R, ws2, w2, pairs, np, km1, kk, wops, lane);
     }
+    if (dense) cq_cpl_fold(P, Q, kk, lane);
     __syncwarp();
 }
 
@@ -651,13 +808,13 @@ __device__ __forceinline__ void cq_tail3c_dispatch(const uint32_t* C, const TriR
                                                    int to, int* mem, uint32_t* R, unsigned long long& n3,
                                                    unsigned long long& n2, unsigned long long& km1,
                                                    unsigned long long& kk, unsigned long long& wops, int lane,
-                                                   bool coop) {
+                                                   bool coop, int cpl) {
     const int w2 = (c + 31) >> 5;
-    if (w2 <= 1) cq_tail3c<1>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop);
-    else if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop);
-    else if (w2 <= 3) cq_tail3c<3>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false);
-    else if (w2 <= 4) cq_tail3c<4>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false);
-    else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false);
+    if (w2 <= 1) cq_tail3c<1>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop, cpl);
+    else if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop, cpl);
+    else if (w2 <= 3) cq_tail3c<3>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
+    else if (w2 <= 4) cq_tail3c<4>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
+    else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
 }
 
 // Split point of a node's remaining children (set bits of C in [from, to))
@@ -766,9 +923,9 @@ __device__ bool cq_walk(const CliqueWalk& a, const CliqueUnit* unit, int root_po
             const int w2 = (c + 31) >> 5;
             if (c > 0 && w2 <= CQ_CW && w2 < w)
                 cq_tail3c_dispatch(Cs, rows, w, c, cur[s], hiv[s], list, a.pairs_u32(), n3, n2, km1, unit_sum, wops,
-                                   lane, a.compact3 == 2);
+                                   lane, a.compact3 == 2, a.cpl);
             else
-                cq_tail3_dispatch(Cs, rows, w, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane);
+                cq_tail3_dispatch(Cs, rows, w, cur[s], hiv[s], a.pairs, n3, n2, km1, unit_sum, wops, lane, a.cpl);
             if (lane == 0) {
                 if (K - 3 >= a.k_lo) cq_wadd(a.ctl, &wcnt[K - 3], n3);
                 if (K - 2 >= a.k_lo) cq_wadd(a.ctl, &wcnt[K - 2], n2);

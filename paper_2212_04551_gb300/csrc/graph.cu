@@ -384,6 +384,7 @@ gpm_config default_config() {
     c.motif_agg_min = 16;
     c.clique_compact3 = 1;
     c.batch_split = 1;
+    c.clique_cpl = 85;
     return c;
 }
 

@@ -6,6 +6,12 @@
 // kernel runs (list_ring.cuh has the record format and the device side).
 // The consumer sees each batch once; the slots are given back to the device
 // before the consumer runs, so production and consumption overlap.
+//
+// While the kernel runs, this thread talks to it only through mapped host
+// words (the count of records taken, the stop request), never through a
+// copy or any other operation on a stream: the runtime may place a second
+// stream on the same hardware queue as the kernel's, and a copy queued there
+// would wait for the kernel, which waits for the copy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,9 +32,9 @@ struct ListJob {
     unsigned long long cap = 0;            // records
     int32_t* host_rec = nullptr;           // mapped pinned ring
     int32_t* dev_rec = nullptr;
-    unsigned long long* host_tail = nullptr;   // pinned: the count the next copy sends
-    unsigned long long* dev_tail = nullptr;    // device: records consumed (host copies)
-    DevBuf head;                           // device: records reserved, records consumed
+    unsigned long long* host_flags = nullptr;  // mapped pinned: [0] records taken, [1] stop request
+    unsigned long long* dev_flags = nullptr;   // the same words, device address
+    DevBuf head;                           // device: records reserved
     int tag_filter = -1;
     unsigned long long max_wait_ns = 0;
     gpm_list_consumer consumer = nullptr;
@@ -44,7 +50,7 @@ struct ListJob {
         // are bounded, so wait for it before the ring goes away
         if (launched) cudaStreamSynchronize(stream);
         if (host_rec) cudaFreeHost(host_rec);
-        if (host_tail) cudaFreeHost(host_tail);
+        if (host_flags) cudaFreeHost(host_flags);
     }
 };
 
@@ -54,7 +60,8 @@ ListRing list_ring_of(const ListJob* j, Control* ctl) {
     r.cap = j->cap;
     r.stride = j->stride;
     r.head = j->head.as<unsigned long long>();
-    r.tail = j->dev_tail;
+    r.tail = j->dev_flags;
+    r.stop = j->dev_flags + 1;
     r.ctl = ctl;
     r.max_wait_ns = j->max_wait_ns;
     r.tag_filter = j->tag_filter;
@@ -73,12 +80,6 @@ std::string list_where(const ListJob* j, const Control& h) {
 // Take the records of the launch that ends at g->ev1, in order, until it has
 // ended and everything it reserved is taken (or the listing stopped / failed).
 void list_drain(ListJob* j, gpm_graph* g, Control* ctl) {
-    cudaStream_t side = nullptr;
-    GPM_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    struct StreamGuard {
-        cudaStream_t s;
-        ~StreamGuard() { cudaStreamDestroy(s); }
-    } guard{side};
     const int words = j->stride - 1;
     const unsigned long long batch = std::min<unsigned long long>(j->cap, 65536);
     std::vector<int32_t> staging((size_t)batch * words);
@@ -101,18 +102,15 @@ void list_drain(ListJob* j, gpm_graph* g, Control* ctl) {
         if (n) {
             idle_polls = 0;
             tail += n;
-            // the slots are free again: tell the device (a copy on the side
-            // stream runs beside the kernel)
-            *j->host_tail = tail;
-            GPM_CUDA(cudaMemcpyAsync(j->dev_tail, j->host_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                                     side));
-            GPM_CUDA(cudaStreamSynchronize(side));
+            // the slots are free again (release: after the reads above)
+            __atomic_store_n(&j->host_flags[0], tail, __ATOMIC_RELEASE);
             j->delivered += n;
             if (j->consumer(staging.data(), (int64_t)n, (int32_t)words, j->user) != 0 && !j->stopped) {
+                // the warps that wait for ring space see the request and end
+                // the listing (ctl->error = DEV_STOPPED); the records after
+                // this batch are not taken
                 j->stopped = true;
-                const int stop = DEV_STOPPED;
-                GPM_CUDA(cudaMemcpyAsync(&ctl->error, &stop, sizeof(int), cudaMemcpyHostToDevice, side));
-                GPM_CUDA(cudaStreamSynchronize(side));
+                __atomic_store_n(&j->host_flags[1], 1ull, __ATOMIC_RELEASE);
             }
             continue;
         }
@@ -123,10 +121,10 @@ void list_drain(ListJob* j, gpm_graph* g, Control* ctl) {
         }
         const cudaError_t q = cudaEventQuery(g->ev1);
         if (q == cudaSuccess) {
+            // the kernel has ended: plain copies are safe now
             int err = 0;
-            GPM_CUDA(cudaMemcpyAsync(&head_end, j->head.ptr, sizeof(head_end), cudaMemcpyDeviceToHost, side));
-            GPM_CUDA(cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, side));
-            GPM_CUDA(cudaStreamSynchronize(side));
+            GPM_CUDA(cudaMemcpy(&head_end, j->head.ptr, sizeof(head_end), cudaMemcpyDeviceToHost));
+            GPM_CUDA(cudaMemcpy(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost));
             if (j->stopped || err) {         // an aborted launch leaves reserved records unwritten
                 const int32_t* rec = j->host_rec + (size_t)(tail % j->cap) * j->stride;
                 j->where = "host took " + std::to_string(tail) + " of " + std::to_string(head_end) +
@@ -177,17 +175,17 @@ void run_list(gpm_graph* g, int app, int k, int32_t pattern, int64_t ring_record
     j.user = user;
     const size_t ring_bytes = sizeof(int32_t) * (size_t)j.cap * j.stride;
     if (cudaHostAlloc(reinterpret_cast<void**>(&j.host_rec), ring_bytes, cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void**>(&j.host_tail), 64, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc(reinterpret_cast<void**>(&j.host_flags), 64, cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         fail(GPM_ENOMEM, "mapped host ring of " + std::to_string(ring_bytes) + " bytes");
     }
     std::memset(j.host_rec, 0, ring_bytes);
-    std::memset(j.host_tail, 0, 64);
+    std::memset(j.host_flags, 0, 64);
     GPM_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&j.dev_rec), j.host_rec, 0));
-    j.head.ensure(2 * sizeof(unsigned long long));
-    j.dev_tail = j.head.as<unsigned long long>() + 1;
+    GPM_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&j.dev_flags), j.host_flags, 0));
+    j.head.ensure(sizeof(unsigned long long));
     cudaStream_t s = g->stream;
-    GPM_CUDA(cudaMemsetAsync(j.head.ptr, 0, 2 * sizeof(unsigned long long), s));
+    GPM_CUDA(cudaMemsetAsync(j.head.ptr, 0, sizeof(unsigned long long), s));
     j.launched = true;
 
     if (app == GPM_APP_MOTIF) {

@@ -9,8 +9,8 @@
 // a device counter, waits (bounded) until the host has consumed far enough
 // for them to be free, writes them, and then stores q + 1 in each record's
 // sequence word (a system-scope release): the host takes records in order
-// once their sequence word matches, and copies the count it has taken into
-// a device word.  The record a
+// once their sequence word matches, and publishes the count it has taken in
+// a mapped host word (beside it, a stop request).  The record a
 // host waits for is never behind a wait of its own writer (a reservation of
 // n <= 32 <= cap records at the host's position always fits), so the two
 // sides cannot block each other.  A stop (the consumer asked for it), an
@@ -29,19 +29,20 @@ struct ListRing {
     unsigned long long cap;                     // records (>= 32)
     int stride;                                 // words per record: 1 + k + 1
     unsigned long long* head;                   // device: records reserved
-    const unsigned long long* tail;             // device: records consumed (written by the host's copies)
+    const unsigned long long* tail;             // mapped host word: records consumed
+    const unsigned long long* stop;             // mapped host word: nonzero once the consumer asked to stop
     Control* ctl;
     unsigned long long max_wait_ns;             // a wait without host progress longer than this fails
     int tag_filter;                             // >= 0: only records with this tag
 };
 
-// The host's count of consumed records: a device word that the host's copy
-// engine overwrites while the kernel runs (acquire: the slots it frees are
-// written after it is read).  The release of a record's sequence word: after
-// the record, at system scope (the host thread reads it from host memory).
-__device__ __forceinline__ unsigned long long lr_load_tail(const unsigned long long* p) {
+// The host's words (count of consumed records, stop request) in mapped host
+// memory: system-scope acquire loads (the slots the count frees are written
+// after it is read).  The release of a record's sequence word: after the
+// record, at system scope (the host thread reads it from host memory).
+__device__ __forceinline__ unsigned long long lr_load_sys(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void lr_publish(int32_t* p, int32_t v) {
@@ -54,10 +55,14 @@ __device__ __forceinline__ unsigned long long lr_reserve(const ListRing& r, int 
     if (*(volatile int*)&r.ctl->error) return ~0ull;
     const unsigned long long pos = atomicAdd(r.head, (unsigned long long)n);
     if (pos + n <= tail_seen + r.cap) return pos;
-    unsigned long long t = lr_load_tail(r.tail);
+    unsigned long long t = lr_load_sys(r.tail);
     unsigned long long last = t, since = gpm_globaltimer();
     while (pos + n > t + r.cap) {
         if (*(volatile int*)&r.ctl->error) return ~0ull;
+        if (lr_load_sys(r.stop)) {          // the consumer asked to stop: end the listing
+            atomicCAS(&r.ctl->error, 0, DEV_STOPPED);
+            return ~0ull;
+        }
         const unsigned long long now = gpm_globaltimer();
         if (t != last) {
             last = t;
@@ -71,7 +76,7 @@ __device__ __forceinline__ unsigned long long lr_reserve(const ListRing& r, int 
             return ~0ull;
         }
         __nanosleep(512);
-        t = lr_load_tail(r.tail);
+        t = lr_load_sys(r.tail);
     }
     tail_seen = t;
     return pos;

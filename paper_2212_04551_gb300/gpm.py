@@ -13,6 +13,7 @@ default stream).
 from __future__ import annotations
 
 import ctypes
+import gc
 import os
 import threading
 
@@ -46,7 +47,8 @@ class gpm_config(ctypes.Structure):
                 ("max_idle_ms", ctypes.c_int32), ("donate", ctypes.c_int32),
                 ("donate_after_us", ctypes.c_int32), ("clique_tail", ctypes.c_int32),
                 ("clique_compact", ctypes.c_int32), ("motif_agg_min", ctypes.c_int32),
-                ("clique_compact3", ctypes.c_int32), ("batch_split", ctypes.c_int32)]
+                ("clique_compact3", ctypes.c_int32), ("batch_split", ctypes.c_int32),
+                ("clique_cpl", ctypes.c_int32)]
 
 
 class gpm_monitor_stats(ctypes.Structure):
@@ -171,6 +173,12 @@ def _array_ptr(a, dtype):
     return arr.ctypes.data, arr, False
 
 
+# listings in progress on this process, and graphs whose destruction waits
+# for them to end
+_LISTING = [0]
+_DEFERRED: list = []
+
+
 class Graph:
     """Owning handle of a gpm_graph (destroyed with the object)."""
 
@@ -183,7 +191,13 @@ class Graph:
 
     def close(self):
         if getattr(self, "handle", None):
-            gpm_graph_destroy(self)
+            if _LISTING[0]:
+                # a listing kernel is running and waits for its consumer: a
+                # destroy now (cudaFree waits for the device) would stall it,
+                # so the handle is destroyed when the listing returns
+                _DEFERRED.append(Graph(self.handle, self._keep))
+            else:
+                gpm_graph_destroy(self)
             self.handle = None
 
     @property
@@ -297,7 +311,23 @@ def gpm_list(g: Graph, app: int, k: int, consumer, pattern: int = -1, ring_recor
 
     cb = GPM_LIST_CONSUMER(_cb)
     out = ctypes.c_uint64()
-    st = load().gpm_list(g, int(app), int(k), int(pattern), int(ring_records), cb, None, ctypes.byref(out))
+    # The consumer runs while the kernel runs and waits for it, so nothing on
+    # this thread may wait for the device meanwhile: no cyclic garbage
+    # collection (finalizers of unreachable graphs would free device memory,
+    # and cudaFree waits for the device), and graphs released during the
+    # call are destroyed after it.
+    gc_on = gc.isenabled()
+    gc.disable()
+    _LISTING[0] += 1
+    try:
+        st = load().gpm_list(g, int(app), int(k), int(pattern), int(ring_records), cb, None, ctypes.byref(out))
+    finally:
+        _LISTING[0] -= 1
+        if gc_on:
+            gc.enable()
+        if not _LISTING[0]:
+            while _DEFERRED:
+                _DEFERRED.pop().close()
     if errors:
         raise errors[0]
     _check(st, "gpm_list")
@@ -505,6 +535,7 @@ def gpm_batch_set_config(b: Batch, **kw) -> None:
     c.motif_agg_min = 16
     c.clique_compact3 = 1
     c.batch_split = 1
+    c.clique_cpl = 85
     for key, val in kw.items():
         setattr(c, key, int(val))
     _check(load().gpm_batch_set_config(b, ctypes.byref(c)), "gpm_batch_set_config")

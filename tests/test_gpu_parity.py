@@ -178,23 +178,27 @@ def test_compacted_tail_dense_graphs(compact):
 
 
 @pytest.mark.parametrize("compact3", [0, 1, 2])
-def test_three_level_tail_modes(compact3):
+@pytest.mark.parametrize("cpl", [0, 1, 85])
+def test_three_level_tail_modes(compact3, cpl):
     """The three-level clique tail (k >= 7) on the full-width rows (0), on
     the node's own members (1), and with the pairs of nodes of at most 64
-    members taken by the whole warp (2): closed forms on K_n and Turan
-    graphs (member sets of 1 to 5 words) and the oracle on dense random
-    graphs and planted blocks."""
+    members taken by the whole warp (2); its deepest level counted per
+    (k-1)-clique (cpl 0), through the non-edges of every node (1), or of
+    nodes at least 85 % dense (85): closed forms on K_n and Turan graphs
+    (member sets of 1 to 5 words; Turan parts give every node non-edges) and
+    the oracle on dense random graphs and planted blocks."""
     for n in (40, 70, 97, 150):
         dg = gpm.graph_from_csr(G.complete(n))
-        gpm.gpm_set_config(dg, clique_compact3=compact3)
+        gpm.gpm_set_config(dg, clique_compact3=compact3, clique_cpl=cpl)
         assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 9)] == [comb(n, k) for k in range(4, 10)], n
-    dg = gpm.graph_from_csr(G.turan(200, 10))
-    gpm.gpm_set_config(dg, clique_compact3=compact3)
-    assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 9)] == [_turan_cliques([20] * 10, k)
-                                                                     for k in range(7, 10)]
-    for g in (G.gnp(120, 0.55, 71), G.sbm(500, 50, 0.6, 0.02, 72)):
+    for n, parts in ((200, 10), (96, 32), (96, 48)):
+        dg = gpm.graph_from_csr(G.turan(n, parts))
+        gpm.gpm_set_config(dg, clique_compact3=compact3, clique_cpl=cpl)
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 9)] == [_turan_cliques([n // parts] * parts, k)
+                                                                         for k in range(7, 10)], (n, parts)
+    for g in (G.gnp(120, 0.55, 71), G.gnp(90, 0.9, 73), G.sbm(500, 50, 0.6, 0.02, 72)):
         dg = gpm.graph_from_csr(g)
-        gpm.gpm_set_config(dg, clique_compact3=compact3, donate_after_us=0, donate_min=2)
+        gpm.gpm_set_config(dg, clique_compact3=compact3, clique_cpl=cpl, donate_after_us=0, donate_min=2)
         want = [O.clique_count(g, k) for k in (7, 8)]
         assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 8)] == want, g.n
         assert [gpm.gpm_clique_count(dg, k) for k in (7, 8)] == want, g.n
