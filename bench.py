@@ -95,6 +95,8 @@ def peaks():
 # (the integer-intrinsic throughput of the CUDA arithmetic-instruction table)
 # x 152 SMs x the maximum SM clock.
 POPC_PER_CLK_PER_SM = 16
+# Instruction issue: 4 schedulers per SM, one warp instruction each per clock.
+ISSUE_PER_CLK_PER_SM = 4
 
 
 def kernel_source_hash(names) -> str:
@@ -106,27 +108,27 @@ def kernel_source_hash(names) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary: str, src_hash: str, units_now: float):
-    """DRAM bytes per launch from a committed ncu summary of the same launch,
-    or None when the kernel source changed since or the launch differs (the
-    clique kernel's DRAM bytes are the per-root row builds, which do not grow
-    with the word operations of deeper k ranges, so they are not scaled)."""
+def profiled_launch(summary: str, src_hash: str, units_now: float) -> dict:
+    """Per-launch counters of the same launch from a committed ncu summary
+    (profiles/<summary>: DRAM bytes, warp instructions executed), or {} when
+    the kernel source changed since or the launch differs (its exact
+    word-operation count identifies it)."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
-        return None
+        return {}
     kv = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_sha") != src_hash:
-        return None
+        return {}
     try:
-        t = float(kv["dram_bytes_per_launch"])
         u = float(kv["units_per_launch"])
+        out = {"dram_bytes": float(kv["dram_bytes_per_launch"]), "warp_inst": float(kv["warp_inst_per_launch"])}
     except (KeyError, ValueError):
-        return None
-    return t if u > 0 and abs(units_now - u) <= 1e-6 * u else None
+        return {}
+    return out if u > 0 and abs(units_now - u) <= 1e-6 * u else {}
 
 
 def golden(name: str):
@@ -849,24 +851,39 @@ def main():
         assert [int(x) for x in c2] == [int(x) for x in counts], "end-to-end counts differ"
     e2e_value = total / (statistics.mean(e2e_ms) / 1000.0)
 
-    # roofline of the dominant kernel (k_clique): ALU-bound on population
-    # counts of candidate words; achieved = word operations per launch (the
-    # kernel counts them exactly) / the launch's CUDA-event time
+    # roofline of the dominant kernel (k_clique), an integer-issue-bound
+    # kernel: warp instructions issued per second against the SMs' issue
+    # slots (4 schedulers x 1 instruction per clock per SM), with the
+    # launch's instruction count from the committed ncu summary of the same
+    # launch (identified by its exact word-operation count) and its time
+    # measured here; beside it the word operations (AND + POPC of 32-bit
+    # candidate words, counted exactly by the kernel) against the POPC rate
     hbm, sm_max, peak_kind = peaks()
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    kern_s = statistics.mean(kern_ms) / 1000.0
     peak_ops = sms * POPC_PER_CLK_PER_SM * sm_max * 1e6
+    peak_issue = sms * ISSUE_PER_CLK_PER_SM * sm_max * 1e6
     wops = statistics.mean(word_ops)
-    achieved = wops / (statistics.mean(kern_ms) / 1000.0)
     src_hash = kernel_source_hash(["clique.cu", "clique_dev.cuh", "common.cuh"])
-    roofline = {"bound": "alu", "kernel": "k_clique", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-                "unit": "Gop/s (32-bit candidate-word AND+POPC)", "frac": achieved / peak_ops,
-                "peak_kind": f"derived: {sms} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz ({peak_kind} clock)",
-                "units_per_launch": wops,
-                "traffic": profiled_traffic(f"k_clique_chunglu1m_k{args.k_lo}_{args.k_hi}.txt", src_hash, wops),
-                "kernel_source_sha": src_hash}
+    prof = profiled_launch(f"k_clique_chunglu1m_k{args.k_lo}_{args.k_hi}.txt", src_hash, wops)
+    word_line = {"achieved": wops / kern_s / 1e9, "peak": peak_ops / 1e9,
+                 "unit": "Gop/s (32-bit candidate-word AND+POPC)", "frac": wops / kern_s / peak_ops,
+                 "peak_kind": f"derived: {sms} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz",
+                 "units_per_launch": wops}
+    if prof:
+        roofline = {"bound": "alu", "kernel": "k_clique", "achieved": prof["warp_inst"] / kern_s / 1e9,
+                    "peak": peak_issue / 1e9, "unit": "G warp instructions/s",
+                    "frac": prof["warp_inst"] / kern_s / peak_issue,
+                    "peak_kind": f"derived: {sms} SMs x {ISSUE_PER_CLK_PER_SM} issue slots/clk x {sm_max:.0f} MHz "
+                                 f"({peak_kind} clock)",
+                    "units_per_launch": prof["warp_inst"], "traffic": prof["dram_bytes"],
+                    "counts_from": f"profiles/k_clique_chunglu1m_k{args.k_lo}_{args.k_hi}.txt (ncu, same launch)",
+                    "word_ops": word_line, "kernel_source_sha": src_hash}
+    else:
+        roofline = {"bound": "alu", "kernel": "k_clique", **word_line, "traffic": None,
+                    "kernel_source_sha": src_hash}
     # HBM: DRAM bytes of the launch (ncu) over its time -- reported beside the
     # ALU roofline to show that memory bandwidth is not what binds the kernel
-    kern_s = statistics.mean(kern_ms) / 1000.0
     traffic = roofline["traffic"]
     hbm_line = {"achieved_gbs": traffic / kern_s / 1e9 if traffic else None, "peak_gbs": hbm,
                 "frac": traffic / kern_s / 1e9 / hbm if traffic else None,

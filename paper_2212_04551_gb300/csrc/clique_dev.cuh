@@ -323,11 +323,9 @@ __device__ __forceinline__ void cq_tail2(const uint32_t* C, const TriRows& rows,
 __device__ __forceinline__ void cq_tail2_dispatch(const uint32_t* C, const TriRows& rows, int w, const int* list,
                                                   int nchild, unsigned long long& km1, unsigned long long& kk,
                                                   unsigned long long& wops, int lane) {
-    if (w <= 1) cq_tail2<1>(C, rows, w, list, nchild, km1, kk, wops, lane);
-    else if (w <= 2) cq_tail2<2>(C, rows, w, list, nchild, km1, kk, wops, lane);
+    // few row widths, for the instruction cache (as cq_tail3c_dispatch)
+    if (w <= 2) cq_tail2<2>(C, rows, w, list, nchild, km1, kk, wops, lane);
     else if (w <= 4) cq_tail2<4>(C, rows, w, list, nchild, km1, kk, wops, lane);
-    else if (w <= 6) cq_tail2<6>(C, rows, w, list, nchild, km1, kk, wops, lane);
-    else if (w <= 8) cq_tail2<8>(C, rows, w, list, nchild, km1, kk, wops, lane);
     else if (w <= 10) cq_tail2<10>(C, rows, w, list, nchild, km1, kk, wops, lane);
     else {
         // wide rows (out-degree > 320): C_i's words are recomputed from shared
@@ -423,8 +421,6 @@ __device__ __forceinline__ void cq_tail2c_dispatch(const uint32_t* C, const TriR
                                                    unsigned long long& kk, unsigned long long& wops, int lane) {
     const int w2 = (c + 31) >> 5;
     if (w2 <= 2) cq_tail2c<2>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
-    else if (w2 <= 3) cq_tail2c<3>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
-    else if (w2 <= 4) cq_tail2c<4>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
     else cq_tail2c<5>(C, rows, w, c, from, to, mem, R, nchild, km1, kk, wops, lane);
 }
 
@@ -636,11 +632,9 @@ __device__ __forceinline__ void cq_tail3_dispatch(const uint32_t* C, const TriRo
                                                   int* pairs, unsigned long long& n3, unsigned long long& n2,
                                                   unsigned long long& km1, unsigned long long& kk,
                                                   unsigned long long& wops, int lane, int cpl) {
-    if (w <= 1) cq_tail3<1>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
-    else if (w <= 2) cq_tail3<2>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
+    // few row widths, for the instruction cache (as cq_tail3c_dispatch)
+    if (w <= 2) cq_tail3<2>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
     else if (w <= 4) cq_tail3<4>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
-    else if (w <= 6) cq_tail3<6>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
-    else if (w <= 8) cq_tail3<8>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
     else cq_tail3<10>(C, rows, w, from, to, pairs, n3, n2, km1, kk, wops, lane, cpl);
 }
 
@@ -809,11 +803,12 @@ __device__ __forceinline__ void cq_tail3c_dispatch(const uint32_t* C, const TriR
                                                    unsigned long long& n2, unsigned long long& km1,
                                                    unsigned long long& kk, unsigned long long& wops, int lane,
                                                    bool coop, int cpl) {
+    // two row widths only: each width is a separate unrolled copy of the
+    // tail, and warps in nodes of different widths would otherwise compete
+    // for the instruction cache (measured: 4..7 2.81 -> 1.69 s against one
+    // copy per width 1..5); narrower nodes run with zero words
     const int w2 = (c + 31) >> 5;
-    if (w2 <= 1) cq_tail3c<1>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop, cpl);
-    else if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop, cpl);
-    else if (w2 <= 3) cq_tail3c<3>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
-    else if (w2 <= 4) cq_tail3c<4>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
+    if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop, cpl);
     else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
 }
 

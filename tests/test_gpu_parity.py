@@ -187,21 +187,32 @@ def test_three_level_tail_modes(compact3, cpl):
     nodes at least 85 % dense (85): closed forms on K_n and Turan graphs
     (member sets of 1 to 5 words; Turan parts give every node non-edges) and
     the oracle on dense random graphs and planted blocks."""
-    for n in (40, 70, 97, 150):
+    for n, k_hi in ((40, 9), (70, 9), (97, 9), (150, 7)):
         dg = gpm.graph_from_csr(G.complete(n))
         gpm.gpm_set_config(dg, clique_compact3=compact3, clique_cpl=cpl)
-        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, 9)] == [comb(n, k) for k in range(4, 10)], n
-    for n, parts in ((200, 10), (96, 32), (96, 48)):
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 4, k_hi)] == [comb(n, k) for k in range(4, k_hi + 1)], n
+    for n, parts, k_hi in ((200, 10, 8), (96, 32, 9), (96, 48, 9)):
         dg = gpm.graph_from_csr(G.turan(n, parts))
         gpm.gpm_set_config(dg, clique_compact3=compact3, clique_cpl=cpl)
-        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 9)] == [_turan_cliques([n // parts] * parts, k)
-                                                                         for k in range(7, 10)], (n, parts)
-    for g in (G.gnp(120, 0.55, 71), G.gnp(90, 0.9, 73), G.sbm(500, 50, 0.6, 0.02, 72)):
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, k_hi)] == [
+            _turan_cliques([n // parts] * parts, k) for k in range(7, k_hi + 1)], (n, parts)
+    for name, g, want in _dense_oracle_7_8():
         dg = gpm.graph_from_csr(g)
         gpm.gpm_set_config(dg, clique_compact3=compact3, clique_cpl=cpl, donate_after_us=0, donate_min=2)
-        want = [O.clique_count(g, k) for k in (7, 8)]
-        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 8)] == want, g.n
-        assert [gpm.gpm_clique_count(dg, k) for k in (7, 8)] == want, g.n
+        assert [int(x) for x in gpm.gpm_clique_count_range(dg, 7, 8)] == want, name
+        assert [gpm.gpm_clique_count(dg, k) for k in (7, 8)] == want, name
+
+
+@functools.lru_cache(maxsize=1)
+def _dense_oracle_7_8():
+    """Dense graphs with their oracle 7- and 8-clique counts (G(44, 0.9):
+    nodes dense enough for the non-edge count; G(120, 0.55) and planted
+    blocks: nodes that take the per-clique count under the default)."""
+    out = []
+    for name, g in (("gnp120", G.gnp(120, 0.55, 71)), ("gnp44", G.gnp(44, 0.9, 73)),
+                    ("sbm500", G.sbm(500, 50, 0.6, 0.02, 72))):
+        out.append((name, g, [O.clique_count(g, k) for k in (7, 8)]))
+    return tuple(out)
 
 
 def test_star_with_large_hub():
