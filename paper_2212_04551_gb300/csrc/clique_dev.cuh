@@ -732,13 +732,16 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
         // holding the rows of members t and t + 32, and for a pair with
         // candidates y adds popc(y & R[t]) when t is in y -- every lane works
         // on every pair, whatever |y|, instead of one lane looping over it
+        // (the second word exists only when the node has two words of
+        // members: one-word nodes run this width too, with rows of stride 1)
+        const bool two = W2 == 2 && w2 == 2;
         const uint32_t ra0 = lane < c ? R[lane * ws2] : 0u;
-        const uint32_t ra1 = (W2 == 2 && lane < c) ? R[lane * ws2 + (W2 == 2 ? 1 : 0)] : 0u;
-        const uint32_t rb1 = (W2 == 2 && lane + 32 < c) ? R[(lane + 32) * ws2 + (W2 == 2 ? 1 : 0)] : 0u;
+        const uint32_t ra1 = (two && lane < c) ? R[lane * ws2 + 1] : 0u;
+        const uint32_t rb1 = (two && lane + 32 < c) ? R[(lane + 32) * ws2 + 1] : 0u;
         unsigned long long npairs = 0, mine = 0, g_all = 0;
         for (int m1 = m_lo; m1 < m_hi; m1++) {
             const uint32_t x0 = R[m1 * ws2];
-            const uint32_t x1 = W2 == 2 ? R[m1 * ws2 + (W2 == 2 ? 1 : 0)] : 0u;
+            const uint32_t x1 = two ? R[m1 * ws2 + 1] : 0u;
 #pragma unroll
             for (int q2 = 0; q2 < W2; q2++) {
                 uint32_t bits = q2 == 0 ? x0 : x1;
@@ -746,7 +749,7 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
                     const int m2 = 32 * q2 + __ffs(bits) - 1;
                     bits &= bits - 1u;
                     const uint32_t y0 = x0 & R[m2 * ws2];
-                    const uint32_t y1 = W2 == 2 ? (x1 & R[m2 * ws2 + (W2 == 2 ? 1 : 0)]) : 0u;
+                    const uint32_t y1 = two ? (x1 & R[m2 * ws2 + 1]) : 0u;
                     npairs++;
                     g_all += (unsigned)(__popc(y0) + __popc(y1));
                     unsigned v = ((y0 >> lane) & 1u) ? (unsigned)(__popc(y0 & ra0) + __popc(y1 & ra1)) : 0u;
