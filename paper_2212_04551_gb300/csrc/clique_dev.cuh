@@ -727,14 +727,14 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
     if (lane == 0) wops += (unsigned long long)c * (unsigned)w2;
     n3 += (unsigned)(m_hi - m_lo);
     const bool dense = cq_cpl_dense(cpl, edges, c);
-    if (W2 <= 2 && coop && !dense) {
+    if (coop && w2 <= 2 && !dense) {
         // at most 64 members: the warp takes the pairs one at a time, lane t
         // holding the rows of members t and t + 32, and for a pair with
         // candidates y adds popc(y & R[t]) when t is in y -- every lane works
         // on every pair, whatever |y|, instead of one lane looping over it
         // (the second word exists only when the node has two words of
         // members: one-word nodes run this width too, with rows of stride 1)
-        const bool two = W2 == 2 && w2 == 2;
+        const bool two = w2 == 2;
         const uint32_t ra0 = lane < c ? R[lane * ws2] : 0u;
         const uint32_t ra1 = (two && lane < c) ? R[lane * ws2 + 1] : 0u;
         const uint32_t rb1 = (two && lane + 32 < c) ? R[(lane + 32) * ws2 + 1] : 0u;
@@ -743,7 +743,7 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
             const uint32_t x0 = R[m1 * ws2];
             const uint32_t x1 = two ? R[m1 * ws2 + 1] : 0u;
 #pragma unroll
-            for (int q2 = 0; q2 < W2; q2++) {
+            for (int q2 = 0; q2 < 2; q2++) {
                 uint32_t bits = q2 == 0 ? x0 : x1;
                 while (bits) {
                     const int m2 = 32 * q2 + __ffs(bits) - 1;
@@ -753,7 +753,7 @@ __device__ __forceinline__ void cq_tail3c(const uint32_t* C, const TriRows& rows
                     npairs++;
                     g_all += (unsigned)(__popc(y0) + __popc(y1));
                     unsigned v = ((y0 >> lane) & 1u) ? (unsigned)(__popc(y0 & ra0) + __popc(y1 & ra1)) : 0u;
-                    if (W2 == 2) v += ((y1 >> lane) & 1u) ? (unsigned)__popc(y1 & rb1) : 0u;
+                    v += ((y1 >> lane) & 1u) ? (unsigned)__popc(y1 & rb1) : 0u;
                     mine += v;
                 }
             }
@@ -806,13 +806,12 @@ __device__ __forceinline__ void cq_tail3c_dispatch(const uint32_t* C, const TriR
                                                    unsigned long long& n2, unsigned long long& km1,
                                                    unsigned long long& kk, unsigned long long& wops, int lane,
                                                    bool coop, int cpl) {
-    // two row widths only: each width is a separate unrolled copy of the
-    // tail, and warps in nodes of different widths would otherwise compete
-    // for the instruction cache (measured: 4..7 2.81 -> 1.69 s against one
-    // copy per width 1..5); narrower nodes run with zero words
+    // one row width: each width is a separate unrolled copy of the tail, and
+    // warps in nodes of different widths compete for the instruction cache
+    // (chunglu1m 4..7: one copy per width 1..5 2.81 s, widths 2 and 5
+    // 1.59 s, width 5 alone 1.34 s); narrower nodes run with zero words
     const int w2 = (c + 31) >> 5;
-    if (w2 <= 2) cq_tail3c<2>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop, cpl);
-    else cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, false, cpl);
+    cq_tail3c<5>(C, rows, w, c, from, to, mem, R, n3, n2, km1, kk, wops, lane, coop && w2 <= 2, cpl);
 }
 
 // Split point of a node's remaining children (set bits of C in [from, to))
