@@ -173,10 +173,12 @@ def _array_ptr(a, dtype):
     return arr.ctypes.data, arr, False
 
 
-# listings in progress on this process, and graphs whose destruction waits
-# for them to end
-_LISTING = [0]
+# listings in progress in this process (and whether the cyclic garbage
+# collector was on before the first of them), and graphs whose destruction
+# waits for them to end
+_LISTING = [0, False]
 _DEFERRED: list = []
+_LISTING_LOCK = threading.Lock()
 
 
 class Graph:
@@ -316,16 +318,20 @@ def gpm_list(g: Graph, app: int, k: int, consumer, pattern: int = -1, ring_recor
     # collection (finalizers of unreachable graphs would free device memory,
     # and cudaFree waits for the device), and graphs released during the
     # call are destroyed after it.
-    gc_on = gc.isenabled()
-    gc.disable()
-    _LISTING[0] += 1
+    with _LISTING_LOCK:
+        if _LISTING[0] == 0:
+            _LISTING[1] = gc.isenabled()
+            gc.disable()
+        _LISTING[0] += 1
     try:
         st = load().gpm_list(g, int(app), int(k), int(pattern), int(ring_records), cb, None, ctypes.byref(out))
     finally:
-        _LISTING[0] -= 1
-        if gc_on:
-            gc.enable()
-        if not _LISTING[0]:
+        with _LISTING_LOCK:
+            _LISTING[0] -= 1
+            last = _LISTING[0] == 0
+            if last and _LISTING[1]:
+                gc.enable()
+        if last:
             while _DEFERRED:
                 _DEFERRED.pop().close()
     if errors:
